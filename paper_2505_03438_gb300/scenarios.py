@@ -1,0 +1,160 @@
+"""Seeded synthetic inputs shared by the GPU library's callers and the oracle.
+
+This module holds no arithmetic of the method (no forces, no cells, no
+integration): it only places particles and draws velocities, with numpy's
+PCG64 generator from a stated seed, so that the GPU path and the CPU oracle
+are fed the very same arrays.  The workloads stand in for the paper's
+md-flexible inputs, which are not available (Sec. 6, Appendix B); their
+shapes follow the homogeneous liquid, the inhomogeneous sphere-in-vapour,
+the batched-replica and the binary-mixture cases of the hot path.
+
+Every scenario is a plain dict:
+  x (N,3) f64, v (N,3) f64, types (N,) i32, box (3,) f64,
+  eps/sigma/rcut (nt,nt) f64, mass (nt,) f64, dt, skin, rebuild, shift, name.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+FCC_BASIS = np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.0], [0.5, 0.0, 0.5], [0.0, 0.5, 0.5]])
+
+
+def fcc_lattice(ncell: int, density: float):
+    """4*ncell^3 sites of a face-centred cubic lattice at the given number density."""
+    a = (4.0 / density) ** (1.0 / 3.0)
+    g = np.stack(np.meshgrid(np.arange(ncell), np.arange(ncell), np.arange(ncell), indexing="ij"), -1)
+    g = g.reshape(-1, 1, 3).astype(np.float64)
+    x = ((g + FCC_BASIS[None]) * a).reshape(-1, 3)
+    box = np.full(3, ncell * a)
+    return x, box
+
+
+def maxwell_boltzmann(n: int, temperature: float, mass, rng) -> np.ndarray:
+    """Gaussian velocities, zero total momentum, rescaled so that
+    sum(m v^2) / (3N - 3) equals the temperature exactly (reduced units)."""
+    mass = np.broadcast_to(np.asarray(mass, np.float64), (n,))
+    v = rng.normal(0.0, 1.0, (n, 3)) * np.sqrt(temperature / mass)[:, None]
+    p = (mass[:, None] * v).sum(0) / mass.sum()
+    v -= p[None, :]
+    if n > 1 and temperature > 0:
+        t_now = float((mass[:, None] * v * v).sum()) / (3 * n - 3)
+        v *= math.sqrt(temperature / t_now)
+    return v
+
+
+def _single_type(box, rc, shift=True):
+    return dict(box=np.asarray(box, np.float64), eps=np.ones((1, 1)), sigma=np.ones((1, 1)),
+                rcut=np.full((1, 1), rc), mass=np.ones(1), shift=shift)
+
+
+def fcc_liquid(ncell: int, density=0.8442, temperature=0.72, seed=1, rc=2.5, skin=0.3,
+               dt=0.005, rebuild=10, jitter=0.0, name="fcc"):
+    """Single-species LJ on an fcc lattice with Maxwell-Boltzmann velocities."""
+    rng = np.random.default_rng(seed)
+    x, box = fcc_lattice(ncell, density)
+    n = x.shape[0]
+    if jitter > 0:
+        x = x + rng.uniform(-jitter, jitter, x.shape)
+        x = np.mod(x, box[None, :])
+    v = maxwell_boltzmann(n, temperature, 1.0, rng)
+    sc = dict(name=name, x=x, v=v, types=np.zeros(n, np.int32), dt=dt, skin=skin, rebuild=rebuild,
+              temperature=temperature, density=density, seed=seed)
+    sc.update(_single_type(box, rc))
+    return sc
+
+
+def small_fcc(seed=1):
+    """Plain-method FP64 case: N = 4000 (10^3 fcc cells x 4), rho 0.8442, T 0.72,
+    r_c 2.5 shifted, cells of side >= r_c (no skin), dt 0.005, 100 NVE steps."""
+    sc = fcc_liquid(10, seed=seed, skin=0.0, rebuild=1, name="fcc_4000_fp64")
+    sc["nsteps"] = 100
+    return sc
+
+
+def liquid_1m(seed=2):
+    """Homogeneous liquid: N = 1,048,576 (64^3 fcc cells x 4), rho 0.8442,
+    T 0.72, r_c 2.5, skin 0.3, rebuild every 10 steps, 1000 steps."""
+    sc = fcc_liquid(64, seed=seed, name="lj_liquid_1m")
+    sc["nsteps"] = 1000
+    return sc
+
+
+def jittered_cubic(n: int, density: float, temperature: float, rng, jitter=0.05):
+    """First n sites (lexicographic) of a simple-cubic lattice with
+    ceil(n^(1/3)) sites per side, each moved by U(-jitter, jitter)."""
+    box_len = (n / density) ** (1.0 / 3.0)
+    side = int(math.ceil(n ** (1.0 / 3.0) - 1e-12))
+    h = box_len / side
+    g = np.stack(np.meshgrid(np.arange(side), np.arange(side), np.arange(side), indexing="ij"), -1).reshape(-1, 3)
+    x = (g[:n].astype(np.float64) + 0.5) * h
+    x = np.mod(x + rng.uniform(-jitter, jitter, x.shape), box_len)
+    v = maxwell_boltzmann(n, temperature, 1.0, rng)
+    return x, v, np.full(3, box_len)
+
+
+def replica_batch(nrep=512, seed=4, nmin=256, nmax=8192, rc=2.5, skin=0.3, dt=0.005, rebuild=10):
+    """Batched replicas: N log-uniform in [nmin, nmax], density U[0.3, 0.9],
+    T U[0.7, 2.0], each a jittered cubic lattice (jitter 0.05)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for r in range(nrep):
+        n = int(round(math.exp(rng.uniform(math.log(nmin), math.log(nmax)))))
+        rho = float(rng.uniform(0.3, 0.9))
+        temp = float(rng.uniform(0.7, 2.0))
+        x, v, box = jittered_cubic(n, rho, temp, rng)
+        sc = dict(name="replica_%d" % r, x=x, v=v, types=np.zeros(n, np.int32), dt=dt, skin=skin,
+                  rebuild=rebuild, temperature=temp, density=rho)
+        sc.update(_single_type(box, rc))
+        out.append(sc)
+    return out
+
+
+def binary_mixture(seed=5, nside=32, density=1.2, temperature=1.0, frac_a=0.8, skin=0.3, dt=0.005,
+                   rebuild=10):
+    """Binary LJ mixture: N = nside^3 on a simple-cubic lattice at density 1.2,
+    A:B = 80:20 (N_A = round(0.8 N), types by seeded permutation),
+    eps_AA 1, sig_AA 1, eps_AB 1.5, sig_AB 0.8, eps_BB 0.5, sig_BB 0.88,
+    cutoff 2.5 sigma_ab per type pair, unit masses."""
+    rng = np.random.default_rng(seed)
+    n = nside ** 3
+    box_len = (n / density) ** (1.0 / 3.0)
+    h = box_len / nside
+    g = np.stack(np.meshgrid(np.arange(nside), np.arange(nside), np.arange(nside), indexing="ij"), -1)
+    x = (g.reshape(-1, 3).astype(np.float64) + 0.5) * h
+    na = int(round(frac_a * n))
+    types = np.ones(n, np.int32)
+    types[rng.permutation(n)[:na]] = 0
+    v = maxwell_boltzmann(n, temperature, 1.0, rng)
+    eps = np.array([[1.0, 1.5], [1.5, 0.5]])
+    sigma = np.array([[1.0, 0.8], [0.8, 0.88]])
+    return dict(name="binary_32768", x=x, v=v, types=types, box=np.full(3, box_len), eps=eps, sigma=sigma,
+                rcut=2.5 * sigma, mass=np.ones(2), shift=True, dt=dt, skin=skin, rebuild=rebuild,
+                temperature=temperature, density=density, seed=seed)
+
+
+def random_gas(n: int, box_len: float, seed: int, min_dist=0.0, rc=2.5, skin=0.3, temperature=1.0):
+    """n uniform random particles in a cubic box (tiny parity cases); with
+    min_dist > 0, candidates closer than min_dist to an accepted one are
+    redrawn (plain O(n^2) rejection, small n only)."""
+    rng = np.random.default_rng(seed)
+    pts = []
+    tries = 0
+    while len(pts) < n:
+        tries += 1
+        if tries > 1000 * n + 1000:
+            raise RuntimeError("random_gas: too dense for rejection placement")
+        c = rng.uniform(0.0, box_len, 3)
+        if min_dist > 0 and pts:
+            d = np.abs(np.asarray(pts) - c)
+            d = np.minimum(d, box_len - d)
+            if (d * d).sum(1).min() < min_dist * min_dist:
+                continue
+        pts.append(c)
+    x = np.asarray(pts, np.float64).reshape(-1, 3)
+    v = maxwell_boltzmann(n, temperature, 1.0, rng)
+    sc = dict(name="gas_%d" % n, x=x, v=v, types=np.zeros(n, np.int32), dt=0.005, skin=skin, rebuild=10,
+              temperature=temperature)
+    sc.update(_single_type(np.full(3, box_len), rc))
+    return sc
