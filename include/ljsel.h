@@ -1,0 +1,240 @@
+/*
+ * ljsel.h -- C ABI of the GB300 library for short-range Lennard-Jones
+ * molecular dynamics with run-time configuration selection, after
+ * "Algorithm Selection in Short-Range Molecular Dynamics Simulations"
+ * (arXiv 2505.03438).
+ *
+ * The paper describes a black-box particle container that a cutoff
+ * simulator drives (Sec. 2.2), which rebuilds its neighbour structure
+ * (Sec. 2.2.1), evaluates forces, advances the simulation (Sec. 2.1) and
+ * selects among algorithmic configurations in tuning phases whose trial
+ * steps still advance the simulation (Sec. 1, Sec. 2.2.5, Sec. 5).  The
+ * calls below are those operations.
+ *
+ * Conventions shared by every call:
+ *  - Every function returns an ljsel_status and never aborts or throws.  On
+ *    failure ljsel_last_error() gives a message (per calling thread).
+ *  - Pointers flagged "host or device" are device pointers when the
+ *    `on_device` argument is non-zero, host pointers otherwise.  All arrays
+ *    are C-contiguous; particle arrays are n x 3 doubles (x, y, z per
+ *    particle) in the caller's input order.  The library re-sorts particles
+ *    internally; that order is never visible to the caller.
+ *  - The library copies inputs into memory it owns and writes outputs into
+ *    caller-owned buffers.  A handle is not thread-safe.
+ *  - Work is enqueued on the stream given at creation (NULL: the legacy
+ *    default stream).  Calls that return values to host memory synchronize
+ *    that stream before returning; ljsel_step does not synchronize.
+ *  - Reduced LJ units throughout (energy eps, length sigma, mass m).
+ */
+#ifndef LJSEL_H
+#define LJSEL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LJSEL_ABI_VERSION 1
+#define LJSEL_MAX_TYPES 4
+
+typedef enum ljsel_status {
+    LJSEL_OK = 0,
+    LJSEL_ERR_ARG = 1,         /* invalid argument or NULL handle                  */
+    LJSEL_ERR_CUDA = 2,        /* a CUDA runtime call failed                       */
+    LJSEL_ERR_OOM = 3,         /* device allocation failed                         */
+    LJSEL_ERR_CAPACITY = 4,    /* neighbour-list capacity overflow not recovered   */
+    LJSEL_ERR_BOX = 5,         /* a box length is below 2 (r_c + skin)             */
+    LJSEL_ERR_NONFINITE = 6,   /* a position, velocity or force became non-finite  */
+    LJSEL_ERR_TIMEOUT = 7,     /* a bounded device-side wait gave up               */
+    LJSEL_ERR_STATE = 8,       /* call not valid in the current state              */
+    LJSEL_ERR_UNSUPPORTED = 9  /* configuration not available for this system      */
+} ljsel_status;
+
+/* Neighbour-identification methods (Sec. 2.2.1, Table 1 in GPU form).       */
+typedef enum ljsel_method {
+    LJSEL_METHOD_LC = 0,       /* linked cells: every step each particle scans the
+                                  particles of the cells within reach (no list)  */
+    LJSEL_METHOD_VL = 1,       /* Verlet lists: per-particle lists of neighbours
+                                  within r_c + skin, rebuilt every R steps        */
+    LJSEL_METHOD_CLUSTER = 2   /* cluster-pair Verlet lists: groups of M spatially
+                                  sorted particles, lists of j-clusters per
+                                  i-cluster (M = 4, 8 or 32)                      */
+} ljsel_method;
+
+/* System parameters.  eps/sigma/rcut are ntypes x ntypes row-major and must
+ * be symmetric; only the first ntypes*ntypes entries are read.            */
+typedef struct ljsel_params {
+    double box[3];             /* periodic orthorhombic box lengths            */
+    int32_t ntypes;            /* 1 .. LJSEL_MAX_TYPES                         */
+    int32_t shift_potential;   /* 1: pair energy shifted to zero at the cutoff */
+    double eps[LJSEL_MAX_TYPES * LJSEL_MAX_TYPES];
+    double sigma[LJSEL_MAX_TYPES * LJSEL_MAX_TYPES];
+    double rcut[LJSEL_MAX_TYPES * LJSEL_MAX_TYPES];   /* cutoff per type pair   */
+    double mass[LJSEL_MAX_TYPES];
+    double skin;               /* Verlet skin (>= 0); list radius r_c + skin   */
+    double dt;                 /* Stormer-Verlet time step                     */
+    int32_t precision;         /* 0: FP32 pair math, FP64 integration and sums;
+                                  1: FP64 everywhere (check path)              */
+    int32_t use_graphs;        /* 1: ljsel_step runs as one CUDA graph with
+                                  device-side rebuild decisions; 0: plain
+                                  stream launches                             */
+} ljsel_params;
+
+/* One algorithmic configuration (the GPU counterpart of a container /
+ * traversal / N3L / cell-size-factor combination, Sec. 2.2).             */
+typedef struct ljsel_config {
+    int32_t method;            /* ljsel_method                                 */
+    int32_t cluster_size;      /* CLUSTER: 4, 8 or 32; ignored otherwise       */
+    int32_t newton3;           /* 1: each pair evaluated once and applied to
+                                  both particles (Sec. 2.1); 0: twice          */
+    int32_t threads_per_unit;  /* threads sharing one particle (LC, VL: 1, 2, 4
+                                  or 8) or one i-cluster (CLUSTER: M, 2M or 4M,
+                                  at most 32 ... 128)                          */
+    int32_t rebuild_interval;  /* R >= 1: rebuild at least every R steps; a
+                                  rebuild also happens as soon as a particle
+                                  has moved skin/2 since the last one          */
+    double csf;                /* cell size factor, 1.0 or 0.5 (Sec. 2.2.1)    */
+} ljsel_config;
+
+/* Live simulation statistics over CSF-1 cell bins (Sec. 4).              */
+typedef struct ljsel_stats {
+    double mean;               /* particles per bin                            */
+    double rel_std;            /* population std / mean                        */
+    double median;             /* mean of the two middle counts if even        */
+    double max;
+    double nbins;
+    double nempty;
+    double skin;
+    double threads;            /* resident GPU threads of the force launch     */
+} ljsel_stats;
+
+/* Counters since creation (host-side copies, refreshed by calls that
+ * synchronize).                                                           */
+typedef struct ljsel_counters {
+    int64_t steps;             /* Verlet steps taken                           */
+    int64_t rebuilds;          /* neighbour-structure rebuilds                 */
+    int64_t early_rebuilds;    /* rebuilds forced by the skin/2 displacement   */
+    int64_t list_entries;      /* entries of the current list (0 for LC)       */
+    int64_t list_capacity;     /* allocated entries                            */
+    int64_t nclusters;         /* i-clusters (CLUSTER)                         */
+    int64_t ncells;            /* cells of the current grid                    */
+    int64_t capacity_retries;  /* list reallocations after an overflow         */
+} ljsel_counters;
+
+/* Autotuner options (Sec. 2.2.5 Full Search, Sec. 5.1 Predictive).       */
+typedef struct ljsel_tuner_opts {
+    int32_t strategy;          /* 0: full search; 1: predictive              */
+    int32_t trial_steps;       /* steps per trial (>= 1); a trial first
+                                  rebuilds, then advances trial_steps steps   */
+    double predict_factor;     /* predictive: trial configs predicted within
+                                  this factor of the best (2.0)               */
+    double blacklist_factor;   /* drop configs measured this much slower than
+                                  the best (10.0); <= 0 disables              */
+    int32_t retrial_phases;    /* predictive: re-trial a config not trialled
+                                  for this many phases (>= 1)                 */
+    int32_t ncandidates;       /* > 0: use candidates[]; 0: the default set   */
+    const ljsel_config *candidates;
+} ljsel_tuner_opts;
+
+/* Result of the last tuning phase.                                        */
+typedef struct ljsel_tuner_report {
+    int32_t phase;             /* tuning phases run so far                    */
+    int32_t ntrialled;         /* configs trialled in the last phase          */
+    int32_t nblacklisted;
+    int32_t chosen_index;      /* index into the candidate set                */
+    double chosen_cost_ms;     /* cost per step of the chosen config          */
+    double phase_ms;           /* wall time of the last phase (all trials)    */
+    double overhead_ms;        /* sum over trials of (trial - chosen) cost    */
+    int64_t trial_steps_total; /* steps advanced by trials in the last phase  */
+} ljsel_tuner_report;
+
+typedef struct ljsel_system_s *ljsel_system;
+
+/* Message of the last failing call on this thread ("" if none).           */
+const char *ljsel_last_error(void);
+int32_t ljsel_abi_version(void);
+
+/* Create a system of n particles (Sec. 2.1).  pos, vel: n x 3 (host or
+ * device per on_device); types: n int32 in [0, ntypes) (host or device;
+ * NULL means all 0).  stream: a cudaStream_t or NULL.  Fails with
+ * LJSEL_ERR_BOX if a box length is below 2 (max r_c + skin), LJSEL_ERR_ARG
+ * for malformed parameters.  The default configuration is VL, N3L off,
+ * one thread per particle, R = 10, CSF 1.  Velocities are at the same time
+ * as positions.  *out receives a handle owned by the caller (free with
+ * ljsel_destroy).                                                         */
+ljsel_status ljsel_create(const ljsel_params *params, int64_t n, const double *pos,
+                          const double *vel, const int32_t *types, int32_t on_device,
+                          void *stream, ljsel_system *out);
+
+ljsel_status ljsel_destroy(ljsel_system s);
+
+/* Select the algorithmic configuration used from now on (Sec. 2.2).  The
+ * next force evaluation rebuilds the neighbour structure.  Returns
+ * LJSEL_ERR_UNSUPPORTED for combinations the library does not provide.     */
+ljsel_status ljsel_set_config(ljsel_system s, const ljsel_config *cfg);
+ljsel_status ljsel_get_config(ljsel_system s, ljsel_config *cfg);
+
+/* Rebuild the neighbour structure now (binning, sorting, lists; Sec.
+ * 2.2.1).  Positions are wrapped into the box first.                     */
+ljsel_status ljsel_rebuild(ljsel_system s);
+
+/* Evaluate forces, potential energy and virial at the current positions
+ * with the current configuration (Sec. 2.1).  forces: n x 3 (host or
+ * device; NULL to skip), in input order.  energy: shifted potential energy
+ * sum over pairs; virial: sum over pairs of r_ij . F_ij (both host double,
+ * NULL to skip).  Synchronizes the stream.                                */
+ljsel_status ljsel_compute(ljsel_system s, double *forces, int32_t on_device,
+                           double *energy, double *virial);
+
+/* Advance nsteps Stormer-Verlet steps (Sec. 2.1) with the current
+ * configuration, rebuilding the neighbour structure every R steps or
+ * earlier when a particle has moved skin/2.  Asynchronous: errors raised on
+ * the device (capacity overflow, non-finite values) are reported by the
+ * next synchronizing call.                                                */
+ljsel_status ljsel_step(ljsel_system s, int64_t nsteps);
+
+/* Copy positions (wrapped into [0, L)) and velocities at the current
+ * integer time step into caller buffers (n x 3, host or device; either may
+ * be NULL).  Synchronizes the stream.                                     */
+ljsel_status ljsel_get_state(ljsel_system s, double *pos, double *vel, int32_t on_device);
+
+/* Replace positions and velocities (n x 3, host or device).               */
+ljsel_status ljsel_set_state(ljsel_system s, const double *pos, const double *vel, int32_t on_device);
+
+/* The positions the pair arithmetic uses (the working-precision copy,
+ * promoted exactly to double, not wrapped), n x 3 in input order.  With
+ * these, the oracle reproduces the pair set bit for bit.                  */
+ljsel_status ljsel_get_work_positions(ljsel_system s, double *pos, int32_t on_device);
+
+/* The set of pairs within the cutoff, exactly as the force evaluation of
+ * the current configuration decides it (Sec. 2.1 neighbours).  ij: host,
+ * 2 x cap int32 (i < j, input indices, unordered); *count receives the
+ * total number of pairs even when it exceeds cap.  Synchronizes.          */
+ljsel_status ljsel_get_pairs(ljsel_system s, int64_t cap, int32_t *ij, int64_t *count);
+
+/* Kinetic and potential energy and virial at the current integer step.    */
+ljsel_status ljsel_get_energy(ljsel_system s, double *epot, double *ekin, double *virial);
+
+/* Live statistics (Sec. 4) of the current positions.                      */
+ljsel_status ljsel_get_stats(ljsel_system s, ljsel_stats *st);
+ljsel_status ljsel_get_counters(ljsel_system s, ljsel_counters *c);
+
+/* Run one tuning phase (Sec. 2.2.5, Sec. 5.1): trial candidate
+ * configurations, each for opts->trial_steps steps that advance the
+ * simulation, keep the one with the lowest cost per step (build time over
+ * R plus force and integration time per step), and select it.  chosen and
+ * report may be NULL.  State (blacklist, history for the predictive
+ * strategy) persists across phases of the same handle.                    */
+ljsel_status ljsel_autotune(ljsel_system s, const ljsel_tuner_opts *opts,
+                            ljsel_config *chosen, ljsel_tuner_report *report);
+
+/* The default candidate set for this system: writes up to cap configs and
+ * returns their number in *count.                                         */
+ljsel_status ljsel_default_candidates(ljsel_system s, int32_t cap, ljsel_config *out, int32_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LJSEL_H */

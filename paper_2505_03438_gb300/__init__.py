@@ -1,0 +1,415 @@
+"""Python binding of libljsel, the GB300 library for short-range LJ molecular
+dynamics with run-time configuration selection (arXiv 2505.03438).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+behind the C ABI of ``include/ljsel.h``.  The functions below carry the same
+names as the C entry points.  Arrays may be numpy arrays (host) or torch
+tensors (host or CUDA); torch is used only for device memory and streams.
+
+The library must have been built (``__graft_entry__.build()`` or
+``python -m paper_2505_03438_gb300.build``); importing a function when the
+shared library is missing raises RuntimeError -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libljsel.so")
+MAX_TYPES = 4
+
+METHOD_LC, METHOD_VL, METHOD_CLUSTER = 0, 1, 2
+METHOD_NAMES = {METHOD_LC: "LC", METHOD_VL: "VL", METHOD_CLUSTER: "CL"}
+
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_CAPACITY", 5: "ERR_BOX",
+          6: "ERR_NONFINITE", 7: "ERR_TIMEOUT", 8: "ERR_STATE", 9: "ERR_UNSUPPORTED"}
+
+
+class LjselError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class ljsel_params(ctypes.Structure):
+    _fields_ = [
+        ("box", ctypes.c_double * 3),
+        ("ntypes", ctypes.c_int32),
+        ("shift_potential", ctypes.c_int32),
+        ("eps", ctypes.c_double * (MAX_TYPES * MAX_TYPES)),
+        ("sigma", ctypes.c_double * (MAX_TYPES * MAX_TYPES)),
+        ("rcut", ctypes.c_double * (MAX_TYPES * MAX_TYPES)),
+        ("mass", ctypes.c_double * MAX_TYPES),
+        ("skin", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("precision", ctypes.c_int32),
+        ("use_graphs", ctypes.c_int32),
+    ]
+
+
+class ljsel_config(ctypes.Structure):
+    _fields_ = [
+        ("method", ctypes.c_int32),
+        ("cluster_size", ctypes.c_int32),
+        ("newton3", ctypes.c_int32),
+        ("threads_per_unit", ctypes.c_int32),
+        ("rebuild_interval", ctypes.c_int32),
+        ("csf", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+    def name(self):
+        m = METHOD_NAMES[self.method]
+        if self.method == METHOD_CLUSTER:
+            m += "%d" % self.cluster_size
+        return "%s-%s-t%d-R%d-csf%g" % (m, "N3L" if self.newton3 else "noN3L", self.threads_per_unit,
+                                         self.rebuild_interval, self.csf)
+
+
+class ljsel_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("mean", "rel_std", "median", "max", "nbins", "nempty", "skin",
+                                                "threads")]
+
+
+class ljsel_counters(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("steps", "rebuilds", "early_rebuilds", "list_entries",
+                                               "list_capacity", "nclusters", "ncells", "capacity_retries")]
+
+
+class ljsel_tuner_opts(ctypes.Structure):
+    _fields_ = [
+        ("strategy", ctypes.c_int32),
+        ("trial_steps", ctypes.c_int32),
+        ("predict_factor", ctypes.c_double),
+        ("blacklist_factor", ctypes.c_double),
+        ("retrial_phases", ctypes.c_int32),
+        ("ncandidates", ctypes.c_int32),
+        ("candidates", ctypes.POINTER(ljsel_config)),
+    ]
+
+
+class ljsel_tuner_report(ctypes.Structure):
+    _fields_ = [
+        ("phase", ctypes.c_int32),
+        ("ntrialled", ctypes.c_int32),
+        ("nblacklisted", ctypes.c_int32),
+        ("chosen_index", ctypes.c_int32),
+        ("chosen_cost_ms", ctypes.c_double),
+        ("phase_ms", ctypes.c_double),
+        ("overhead_ms", ctypes.c_double),
+        ("trial_steps_total", ctypes.c_int64),
+    ]
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "ljsel_last_error": ([], ctypes.c_char_p),
+    "ljsel_abi_version": ([], ctypes.c_int32),
+    "ljsel_create": ([ctypes.POINTER(ljsel_params), ctypes.c_int64, _P, _P, _P, ctypes.c_int32, _P,
+                      ctypes.POINTER(_P)], ctypes.c_int),
+    "ljsel_destroy": ([_P], ctypes.c_int),
+    "ljsel_set_config": ([_P, ctypes.POINTER(ljsel_config)], ctypes.c_int),
+    "ljsel_get_config": ([_P, ctypes.POINTER(ljsel_config)], ctypes.c_int),
+    "ljsel_rebuild": ([_P], ctypes.c_int),
+    "ljsel_compute": ([_P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+                      ctypes.c_int),
+    "ljsel_step": ([_P, ctypes.c_int64], ctypes.c_int),
+    "ljsel_get_state": ([_P, _P, _P, ctypes.c_int32], ctypes.c_int),
+    "ljsel_set_state": ([_P, _P, _P, ctypes.c_int32], ctypes.c_int),
+    "ljsel_get_work_positions": ([_P, _P, ctypes.c_int32], ctypes.c_int),
+    "ljsel_get_pairs": ([_P, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "ljsel_get_energy": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                          ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "ljsel_get_stats": ([_P, ctypes.POINTER(ljsel_stats)], ctypes.c_int),
+    "ljsel_get_counters": ([_P, ctypes.POINTER(ljsel_counters)], ctypes.c_int),
+    "ljsel_autotune": ([_P, ctypes.POINTER(ljsel_tuner_opts), ctypes.POINTER(ljsel_config),
+                        ctypes.POINTER(ljsel_tuner_report)], ctypes.c_int),
+    "ljsel_default_candidates": ([_P, ctypes.c_int32, ctypes.POINTER(ljsel_config), ctypes.POINTER(ctypes.c_int32)],
+                                 ctypes.c_int),
+}
+EXPORTED = tuple(_SIGS)
+_lib = None
+
+
+def lib():
+    """Load libljsel.so (raises RuntimeError when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libljsel.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(st):
+    if st != 0:
+        raise LjselError(st, lib().ljsel_last_error().decode())
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or torch tensor (C-contiguous)."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def make_params(box, eps=1.0, sigma=1.0, rcut=2.5, mass=1.0, skin=0.3, dt=0.005, shift=True, precision=0,
+                use_graphs=True) -> ljsel_params:
+    eps = np.atleast_2d(np.asarray(eps, np.float64))
+    sigma = np.atleast_2d(np.asarray(sigma, np.float64))
+    nt = eps.shape[0]
+    rcut = np.asarray(rcut, np.float64)
+    if rcut.ndim == 0:
+        rcut = np.full((nt, nt), float(rcut))
+    mass = np.broadcast_to(np.asarray(mass, np.float64), (nt,))
+    p = ljsel_params()
+    box = np.broadcast_to(np.asarray(box, np.float64), (3,))
+    for d in range(3):
+        p.box[d] = float(box[d])
+    p.ntypes = nt
+    p.shift_potential = 1 if shift else 0
+    for a in range(nt):
+        p.mass[a] = float(mass[a])
+        for b in range(nt):
+            p.eps[a * nt + b] = float(eps[a, b])
+            p.sigma[a * nt + b] = float(sigma[a, b])
+            p.rcut[a * nt + b] = float(rcut[a, b])
+    p.skin = float(skin)
+    p.dt = float(dt)
+    p.precision = int(precision)
+    p.use_graphs = 1 if use_graphs else 0
+    return p
+
+
+def make_config(method="VL", cluster_size=1, newton3=False, threads_per_unit=1, rebuild_interval=10, csf=1.0):
+    c = ljsel_config()
+    c.method = {"LC": METHOD_LC, "VL": METHOD_VL, "CL": METHOD_CLUSTER, "CLUSTER": METHOD_CLUSTER}.get(method, method)
+    c.cluster_size = int(cluster_size)
+    c.newton3 = 1 if newton3 else 0
+    c.threads_per_unit = int(threads_per_unit)
+    c.rebuild_interval = int(rebuild_interval)
+    c.csf = float(csf)
+    return c
+
+
+# --- the C entry points, same names ------------------------------------------
+
+def ljsel_last_error() -> str:
+    return lib().ljsel_last_error().decode()
+
+
+def ljsel_abi_version() -> int:
+    return int(lib().ljsel_abi_version())
+
+
+def ljsel_create(params: ljsel_params, n, pos, vel, types=None, stream=None):
+    pp, dev = _ptr(pos)
+    vp, dv = _ptr(vel)
+    tp, dt = _ptr(types)
+    if not (dev == dv and (types is None or dt == dev)):
+        raise ValueError("pos, vel and types must all be host or all be device arrays")
+    h = ctypes.c_void_p()
+    _check(lib().ljsel_create(ctypes.byref(params), int(n), pp, vp, tp, dev, stream, ctypes.byref(h)))
+    return h
+
+
+def ljsel_destroy(h):
+    _check(lib().ljsel_destroy(h))
+
+
+def ljsel_set_config(h, cfg: ljsel_config):
+    _check(lib().ljsel_set_config(h, ctypes.byref(cfg)))
+
+
+def ljsel_get_config(h) -> ljsel_config:
+    c = ljsel_config()
+    _check(lib().ljsel_get_config(h, ctypes.byref(c)))
+    return c
+
+
+def ljsel_rebuild(h):
+    _check(lib().ljsel_rebuild(h))
+
+
+def ljsel_compute(h, forces=None):
+    e = ctypes.c_double()
+    w = ctypes.c_double()
+    fp, dev = _ptr(forces)
+    _check(lib().ljsel_compute(h, fp, dev, ctypes.byref(e), ctypes.byref(w)))
+    return e.value, w.value
+
+
+def ljsel_step(h, nsteps):
+    _check(lib().ljsel_step(h, int(nsteps)))
+
+
+def ljsel_get_state(h, pos=None, vel=None):
+    pp, d1 = _ptr(pos)
+    vp, d2 = _ptr(vel)
+    if pos is not None and vel is not None and d1 != d2:
+        raise ValueError("pos and vel must be both host or both device")
+    _check(lib().ljsel_get_state(h, pp, vp, d1 if pos is not None else d2))
+
+
+def ljsel_set_state(h, pos=None, vel=None):
+    pp, d1 = _ptr(pos)
+    vp, d2 = _ptr(vel)
+    if pos is not None and vel is not None and d1 != d2:
+        raise ValueError("pos and vel must be both host or both device")
+    _check(lib().ljsel_set_state(h, pp, vp, d1 if pos is not None else d2))
+
+
+def ljsel_get_work_positions(h, pos):
+    p, d = _ptr(pos)
+    _check(lib().ljsel_get_work_positions(h, p, d))
+
+
+def ljsel_get_pairs(h, cap):
+    buf = np.zeros((max(int(cap), 1), 2), np.int32)
+    cnt = ctypes.c_int64()
+    _check(lib().ljsel_get_pairs(h, int(cap), buf.ctypes.data, ctypes.byref(cnt)))
+    return buf[:min(cnt.value, int(cap))], cnt.value
+
+
+def ljsel_get_energy(h):
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().ljsel_get_energy(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def ljsel_get_stats(h) -> dict:
+    s = ljsel_stats()
+    _check(lib().ljsel_get_stats(h, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in s._fields_}
+
+
+def ljsel_get_counters(h) -> dict:
+    c = ljsel_counters()
+    _check(lib().ljsel_get_counters(h, ctypes.byref(c)))
+    return {k: getattr(c, k) for k, _ in c._fields_}
+
+
+def ljsel_default_candidates(h):
+    cnt = ctypes.c_int32()
+    _check(lib().ljsel_default_candidates(h, 0, None, ctypes.byref(cnt)))
+    arr = (ljsel_config * max(cnt.value, 1))()
+    _check(lib().ljsel_default_candidates(h, cnt.value, arr, ctypes.byref(cnt)))
+    return [arr[k] for k in range(cnt.value)]
+
+
+def ljsel_autotune(h, strategy=0, trial_steps=10, predict_factor=2.0, blacklist_factor=10.0, retrial_phases=4,
+                   candidates=None):
+    o = ljsel_tuner_opts()
+    o.strategy = int(strategy)
+    o.trial_steps = int(trial_steps)
+    o.predict_factor = float(predict_factor)
+    o.blacklist_factor = float(blacklist_factor)
+    o.retrial_phases = int(retrial_phases)
+    arr = None
+    if candidates:
+        arr = (ljsel_config * len(candidates))(*candidates)
+        o.ncandidates = len(candidates)
+        o.candidates = arr
+    chosen = ljsel_config()
+    rep = ljsel_tuner_report()
+    _check(lib().ljsel_autotune(h, ctypes.byref(o), ctypes.byref(chosen), ctypes.byref(rep)))
+    return chosen, {k: getattr(rep, k) for k, _ in rep._fields_}
+
+
+class System:
+    """Owner of one ljsel handle (destroyed with the object); marshalling only."""
+
+    def __init__(self, scenario=None, *, x=None, v=None, types=None, box=None, eps=None, sigma=None, rcut=None,
+                 mass=None, skin=None, dt=None, shift=None, precision=0, use_graphs=True, stream=None):
+        sc = dict(scenario or {})
+        pick = lambda val, key, default: val if val is not None else sc.get(key, default)
+        x, v, types = pick(x, "x", None), pick(v, "v", None), pick(types, "types", None)
+        box = pick(box, "box", None)
+        self.params = make_params(box, pick(eps, "eps", 1.0), pick(sigma, "sigma", 1.0), pick(rcut, "rcut", 2.5),
+                                  pick(mass, "mass", 1.0), pick(skin, "skin", 0.3), pick(dt, "dt", 0.005),
+                                  pick(shift, "shift", True), precision, use_graphs)
+        x = np.ascontiguousarray(x, np.float64) if isinstance(x, np.ndarray) else x
+        v = np.ascontiguousarray(v, np.float64) if isinstance(v, np.ndarray) else v
+        if isinstance(types, np.ndarray):
+            types = np.ascontiguousarray(types, np.int32)
+        self.n = int(x.shape[0])
+        self.h = ljsel_create(self.params, self.n, x, v, types, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            ljsel_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_config(self, cfg=None, **kw):
+        ljsel_set_config(self.h, cfg if cfg is not None else make_config(**kw))
+
+    def config(self):
+        return ljsel_get_config(self.h)
+
+    def compute(self):
+        F = np.zeros((self.n, 3))
+        e, w = ljsel_compute(self.h, F)
+        return F, e, w
+
+    def step(self, nsteps):
+        ljsel_step(self.h, nsteps)
+
+    def state(self):
+        x = np.zeros((self.n, 3))
+        v = np.zeros((self.n, 3))
+        ljsel_get_state(self.h, x, v)
+        return x, v
+
+    def set_state(self, x, v):
+        ljsel_set_state(self.h, np.ascontiguousarray(x, np.float64), np.ascontiguousarray(v, np.float64))
+
+    def work_positions(self):
+        x = np.zeros((self.n, 3))
+        ljsel_get_work_positions(self.h, x)
+        return x
+
+    def pairs(self, cap=None):
+        if cap is None:
+            _, cnt = ljsel_get_pairs(self.h, 0)
+            cap = cnt
+        p, cnt = ljsel_get_pairs(self.h, cap)
+        return p, cnt
+
+    def energy(self):
+        return ljsel_get_energy(self.h)
+
+    def stats(self):
+        return ljsel_get_stats(self.h)
+
+    def counters(self):
+        return ljsel_get_counters(self.h)
+
+    def autotune(self, **kw):
+        return ljsel_autotune(self.h, **kw)
+
+    def rebuild(self):
+        ljsel_rebuild(self.h)

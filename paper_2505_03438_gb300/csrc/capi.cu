@@ -1,0 +1,596 @@
+// capi.cu -- the extern "C" entry points of include/ljsel.h, the live
+// statistics of Sec. 4 and the tuning strategies of Sec. 2.2.5 and Sec. 5.1.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "system.h"
+
+using namespace ljsel;
+
+#define CK(call)                                                                                    \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) {                                                                    \
+            set_error(std::string("CUDA error in ") + #call + ": " + cudaGetErrorString(e_));       \
+            return e_ == cudaErrorMemoryAllocation ? LJSEL_ERR_OOM : LJSEL_ERR_CUDA;                \
+        }                                                                                           \
+    } while (0)
+#define TRY(expr)                         \
+    do {                                  \
+        ljsel_status s_ = (expr);         \
+        if (s_ != LJSEL_OK) return s_;    \
+    } while (0)
+
+namespace {
+
+template <typename F> ljsel_status dispatch(System *s, F &&f) {
+    if (s->precision) return f((double)0);
+    return f((float)0);
+}
+
+// Bin counts over CSF-1 cell bins (side >= r_c,max + skin, stretched to the
+// box) of the wrapped FP64 positions.
+__global__ void k_bin_counts(const double *X, int n, const int *nb, const double *side, int *counts) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c[3];
+    for (int d = 0; d < 3; ++d) {
+        long long k = (long long)floor(X[3 * i + d] / side[d]);
+        k %= nb[d];
+        if (k < 0) k += nb[d];
+        c[d] = (int)k;
+    }
+    atomicAdd(&counts[(c[2] * nb[1] + c[1]) * nb[0] + c[0]], 1);
+}
+
+ljsel_config default_config(const ljsel_params &p) {
+    ljsel_config c{};
+    c.method = LJSEL_METHOD_VL;
+    c.cluster_size = 1;
+    c.newton3 = 0;
+    c.threads_per_unit = 1;
+    c.rebuild_interval = p.skin > 0 ? 10 : 1;
+    c.csf = 1.0;
+    return c;
+}
+
+bool same_cfg(const ljsel_config &a, const ljsel_config &b) {
+    return a.method == b.method && a.newton3 == b.newton3 && a.threads_per_unit == b.threads_per_unit &&
+           a.rebuild_interval == b.rebuild_interval && a.csf == b.csf &&
+           (a.method != LJSEL_METHOD_CLUSTER || a.cluster_size == b.cluster_size);
+}
+
+std::vector<ljsel_config> default_candidates(const System &s) {
+    std::vector<ljsel_config> v;
+    const int R = s.cfg.rebuild_interval;
+    auto add = [&](int method, int M, int n3, int t, double csf, int r) {
+        ljsel_config c{};
+        c.method = method; c.cluster_size = M; c.newton3 = n3; c.threads_per_unit = t; c.csf = csf;
+        c.rebuild_interval = s.params.skin > 0 ? r : 1;
+        if (validate_config(s, &c) == LJSEL_OK) v.push_back(c);
+    };
+    for (int n3 = 0; n3 <= 1; ++n3)
+        for (double csf : {1.0, 0.5}) add(LJSEL_METHOD_LC, 1, n3, 1, csf, R);
+    for (int t : {1, 2, 4, 8}) add(LJSEL_METHOD_VL, 1, 0, t, 1.0, R);
+    for (int t : {1, 4}) add(LJSEL_METHOD_VL, 1, 1, t, 1.0, R);
+    add(LJSEL_METHOD_VL, 1, 0, 1, 1.0, 2 * R);
+    add(LJSEL_METHOD_VL, 1, 0, 2, 1.0, 2 * R);
+    for (int M : {4, 8, 32}) {
+        for (int t = M; t <= 32; t *= 2) add(LJSEL_METHOD_CLUSTER, M, 0, t, 1.0, R);
+        add(LJSEL_METHOD_CLUSTER, M, 1, M, 1.0, R);
+    }
+    return v;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ljsel_last_error(void) { return last_error(); }
+int32_t ljsel_abi_version(void) { return LJSEL_ABI_VERSION; }
+
+ljsel_status ljsel_create(const ljsel_params *params, int64_t n, const double *pos, const double *vel,
+                          const int32_t *types, int32_t on_device, void *stream, ljsel_system *out) {
+    set_error("");
+    if (!out) { set_error("out is NULL"); return LJSEL_ERR_ARG; }
+    *out = nullptr;
+    TRY(validate_params(params));
+    if (n < 1 || n >= (int64_t)JMASK) { set_error("n must be in [1, 2^27)"); return LJSEL_ERR_ARG; }
+    if (!pos || !vel) { set_error("pos and vel are required"); return LJSEL_ERR_ARG; }
+    System *s = new (std::nothrow) System();
+    if (!s) { set_error("host allocation failed"); return LJSEL_ERR_OOM; }
+    s->params = *params;
+    s->n = (int)n;
+    s->precision = params->precision;
+    s->stream = (cudaStream_t)stream;
+    s->cfg = default_config(*params);
+    auto fail = [&](ljsel_status st) { delete s; return st; };
+    if (cudaHostAlloc((void **)&s->h_ctrl, sizeof(Ctrl), cudaHostAllocDefault) != cudaSuccess) {
+        set_error("pinned allocation failed");
+        return fail(LJSEL_ERR_CUDA);
+    }
+    memset(s->h_ctrl, 0, sizeof(Ctrl));
+    if (cudaEventCreate(&s->ev_a) != cudaSuccess || cudaEventCreate(&s->ev_b) != cudaSuccess) {
+        set_error("event creation failed");
+        return fail(LJSEL_ERR_CUDA);
+    }
+    ljsel_status st = s->alloc_base();
+    if (st != LJSEL_OK) return fail(st);
+    st = s->apply_config();
+    if (st != LJSEL_OK) return fail(st);
+    // type check and staging of host inputs
+    std::vector<int32_t> ht;
+    if (types) {
+        ht.resize(n);
+        if (on_device) {
+            if (cudaMemcpy(ht.data(), types, n * 4, cudaMemcpyDeviceToHost) != cudaSuccess) { set_error("types copy failed"); return fail(LJSEL_ERR_CUDA); }
+        } else {
+            memcpy(ht.data(), types, n * 4);
+        }
+        for (int64_t i = 0; i < n; ++i)
+            if (ht[i] < 0 || ht[i] >= params->ntypes) { set_error("a type is outside [0, ntypes)"); return fail(LJSEL_ERR_ARG); }
+    }
+    const size_t nb = (size_t)n * 3 * sizeof(double);
+    const double *dpos = pos, *dvel = vel;
+    const int32_t *dtyp = types;
+    if (!on_device) {
+        st = s->b_io.ensure(2 * nb + (size_t)n * 4);
+        if (st != LJSEL_OK) return fail(st);
+        char *io = (char *)s->b_io.ptr;
+        if (cudaMemcpyAsync(io, pos, nb, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+            cudaMemcpyAsync(io + nb, vel, nb, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
+            set_error("input copy failed");
+            return fail(LJSEL_ERR_CUDA);
+        }
+        dpos = (const double *)io;
+        dvel = (const double *)(io + nb);
+        if (types) {
+            if (cudaMemcpyAsync(io + 2 * nb, types, (size_t)n * 4, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
+                set_error("input copy failed");
+                return fail(LJSEL_ERR_CUDA);
+            }
+            dtyp = (const int32_t *)(io + 2 * nb);
+        }
+    }
+    auto imp = [&](auto z) -> ljsel_status {
+        using R = decltype(z);
+        Dev<R> S;
+        s->fill_dev(S);
+        launch_import_state(S, dpos, dvel, dtyp, 1, s->stream);
+        return LJSEL_OK;
+    };
+    dispatch(s, imp);
+    st = s->cmd(CMD_INTERVAL, s->cfg.rebuild_interval);
+    if (st == LJSEL_OK) st = s->cmd(CMD_REBUILD, 0);
+    if (st == LJSEL_OK) st = s->cmd(CMD_HALF_KICK, 1);
+    if (st == LJSEL_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) { set_error(cudaGetErrorString(cudaGetLastError())); st = LJSEL_ERR_CUDA; }
+    if (st != LJSEL_OK) return fail(st);
+    *out = reinterpret_cast<ljsel_system>(s);
+    return LJSEL_OK;
+}
+
+ljsel_status ljsel_destroy(ljsel_system h) {
+    System *s = (System *)h;
+    if (!s) return LJSEL_OK;
+    cudaStreamSynchronize(s->stream);
+    delete s;
+    return LJSEL_OK;
+}
+
+ljsel_status ljsel_set_config(ljsel_system h, const ljsel_config *cfg) {
+    System *s = (System *)h;
+    if (!s) { set_error("NULL handle"); return LJSEL_ERR_ARG; }
+    TRY(validate_config(*s, cfg));
+    ljsel_config c = *cfg;
+    if (c.method != LJSEL_METHOD_CLUSTER) c.cluster_size = 1;
+    s->cfg = c;
+    return s->apply_config();
+}
+
+ljsel_status ljsel_get_config(ljsel_system h, ljsel_config *cfg) {
+    System *s = (System *)h;
+    if (!s || !cfg) { set_error("NULL argument"); return LJSEL_ERR_ARG; }
+    *cfg = s->cfg;
+    return LJSEL_OK;
+}
+
+ljsel_status ljsel_rebuild(ljsel_system h) {
+    System *s = (System *)h;
+    if (!s) { set_error("NULL handle"); return LJSEL_ERR_ARG; }
+    s->structure_dirty = true;
+    return dispatch(s, [&](auto z) { return s->ensure_structure<decltype(z)>(); });
+}
+
+ljsel_status ljsel_compute(ljsel_system h, double *forces, int32_t on_device, double *energy, double *virial) {
+    System *s = (System *)h;
+    if (!s) { set_error("NULL handle"); return LJSEL_ERR_ARG; }
+    return dispatch(s, [&](auto z) -> ljsel_status {
+        using R = decltype(z);
+        TRY(s->compute_forces<R>(true));
+        Dev<R> S;
+        s->fill_dev(S);
+        if (forces) {
+            if (on_device) {
+                launch_export_forces(S, forces, s->stream);
+            } else {
+                TRY(s->b_io.ensure((size_t)s->n * 3 * sizeof(double)));
+                launch_export_forces(S, (double *)s->b_io.ptr, s->stream);
+                CK(cudaMemcpyAsync(forces, s->b_io.ptr, (size_t)s->n * 3 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+            }
+        }
+        if (s->cfg.newton3) launch_zero_force(S, s->stream);
+        CK(cudaGetLastError());
+        TRY(s->read_ctrl());
+        TRY(s->check_device_errors());
+        if (energy) *energy = s->h_ctrl->epot;
+        if (virial) *virial = s->h_ctrl->virial;
+        return LJSEL_OK;
+    });
+}
+
+ljsel_status ljsel_step(ljsel_system h, int64_t nsteps) {
+    System *s = (System *)h;
+    if (!s) { set_error("NULL handle"); return LJSEL_ERR_ARG; }
+    if (nsteps < 0) { set_error("nsteps must be >= 0"); return LJSEL_ERR_ARG; }
+    return dispatch(s, [&](auto z) { return s->advance<decltype(z)>(nsteps); });
+}
+
+ljsel_status ljsel_get_state(ljsel_system h, double *pos, double *vel, int32_t on_device) {
+    System *s = (System *)h;
+    if (!s) { set_error("NULL handle"); return LJSEL_ERR_ARG; }
+    return dispatch(s, [&](auto z) -> ljsel_status {
+        using R = decltype(z);
+        if (vel) TRY(s->sync_velocities<R>());
+        Dev<R> S;
+        s->fill_dev(S);
+        const size_t nb = (size_t)s->n * 3 * sizeof(double);
+        if (on_device) {
+            launch_export_state(S, pos, vel, 1, s->stream);
+        } else {
+            TRY(s->b_io.ensure(2 * nb));
+            double *dp = pos ? (double *)s->b_io.ptr : nullptr;
+            double *dv = vel ? (double *)((char *)s->b_io.ptr + nb) : nullptr;
+            launch_export_state(S, dp, dv, 1, s->stream);
+            if (pos) CK(cudaMemcpyAsync(pos, dp, nb, cudaMemcpyDeviceToHost, s->stream));
+            if (vel) CK(cudaMemcpyAsync(vel, dv, nb, cudaMemcpyDeviceToHost, s->stream));
+        }
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(s->stream));
+        return LJSEL_OK;
+    });
+}
+
+ljsel_status ljsel_set_state(ljsel_system h, const double *pos, const double *vel, int32_t on_device) {
+    System *s = (System *)h;
+    if (!s) { set_error("NULL handle"); return LJSEL_ERR_ARG; }
+    return dispatch(s, [&](auto z) -> ljsel_status {
+        using R = decltype(z);
+        const size_t nb = (size_t)s->n * 3 * sizeof(double);
+        const double *dp = pos, *dv = vel;
+        if (!on_device) {
+            TRY(s->b_io.ensure(2 * nb));
+            if (pos) { CK(cudaMemcpyAsync(s->b_io.ptr, pos, nb, cudaMemcpyHostToDevice, s->stream)); dp = (const double *)s->b_io.ptr; }
+            if (vel) { CK(cudaMemcpyAsync((char *)s->b_io.ptr + nb, vel, nb, cudaMemcpyHostToDevice, s->stream)); dv = (const double *)((char *)s->b_io.ptr + nb); }
+        }
+        Dev<R> S;
+        s->fill_dev(S);
+        launch_import_state(S, dp, dv, nullptr, 0, s->stream);
+        TRY(s->cmd(CMD_REBUILD, 0));
+        TRY(s->cmd(CMD_HALF_KICK, 1));
+        s->synced = true;
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(s->stream));
+        return LJSEL_OK;
+    });
+}
+
+ljsel_status ljsel_get_work_positions(ljsel_system h, double *pos, int32_t on_device) {
+    System *s = (System *)h;
+    if (!s || !pos) { set_error("NULL argument"); return LJSEL_ERR_ARG; }
+    return dispatch(s, [&](auto z) -> ljsel_status {
+        using R = decltype(z);
+        Dev<R> S;
+        s->fill_dev(S);
+        const size_t nb = (size_t)s->n * 3 * sizeof(double);
+        if (on_device) {
+            launch_export_work_pos(S, pos, s->stream);
+        } else {
+            TRY(s->b_io.ensure(nb));
+            launch_export_work_pos(S, (double *)s->b_io.ptr, s->stream);
+            CK(cudaMemcpyAsync(pos, s->b_io.ptr, nb, cudaMemcpyDeviceToHost, s->stream));
+        }
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(s->stream));
+        return LJSEL_OK;
+    });
+}
+
+ljsel_status ljsel_get_pairs(ljsel_system h, int64_t cap, int32_t *ij, int64_t *count) {
+    System *s = (System *)h;
+    if (!s || !count || cap < 0 || (cap > 0 && !ij)) { set_error("invalid argument"); return LJSEL_ERR_ARG; }
+    return dispatch(s, [&](auto z) -> ljsel_status {
+        using R = decltype(z);
+        TRY(s->ensure_structure<R>());
+        Dev<R> S;
+        s->fill_dev(S);
+        int2 *buf = nullptr;
+        if (cap > 0) CK(cudaMalloc(&buf, (size_t)cap * sizeof(int2)));
+        TRY(s->cmd(CMD_RESET_PAIRS, 0));
+        launch_force(S, s->cfg, MODE_PAIRS, false, buf, cap, s->stream);
+        cudaError_t e = cudaGetLastError();
+        ljsel_status st = LJSEL_OK;
+        if (e == cudaSuccess) st = s->read_ctrl();
+        long long got = (long long)s->h_ctrl->npairs;
+        if (e == cudaSuccess && st == LJSEL_OK && cap > 0)
+            e = cudaMemcpy(ij, buf, (size_t)std::min<long long>(got, cap) * sizeof(int2), cudaMemcpyDeviceToHost);
+        if (buf) cudaFree(buf);
+        if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return LJSEL_ERR_CUDA; }
+        if (st != LJSEL_OK) return st;
+        *count = got;
+        return LJSEL_OK;
+    });
+}
+
+ljsel_status ljsel_get_energy(ljsel_system h, double *epot, double *ekin, double *virial) {
+    System *s = (System *)h;
+    if (!s) { set_error("NULL handle"); return LJSEL_ERR_ARG; }
+    return dispatch(s, [&](auto z) -> ljsel_status {
+        using R = decltype(z);
+        TRY(s->sync_velocities<R>());
+        TRY(s->compute_forces<R>(true));
+        Dev<R> S;
+        s->fill_dev(S);
+        launch_kinetic(S, s->stream);
+        if (s->cfg.newton3) launch_zero_force(S, s->stream);
+        CK(cudaGetLastError());
+        TRY(s->read_ctrl());
+        TRY(s->check_device_errors());
+        if (epot) *epot = s->h_ctrl->epot;
+        if (ekin) *ekin = s->h_ctrl->ekin;
+        if (virial) *virial = s->h_ctrl->virial;
+        return LJSEL_OK;
+    });
+}
+
+ljsel_status ljsel_get_stats(ljsel_system h, ljsel_stats *st) {
+    System *s = (System *)h;
+    if (!s || !st) { set_error("NULL argument"); return LJSEL_ERR_ARG; }
+    double rcm = 0;
+    for (int t = 0; t < s->params.ntypes * s->params.ntypes; ++t) rcm = std::max(rcm, s->params.rcut[t]);
+    const double bin_min = rcm + s->params.skin;
+    int nb[3];
+    double side[3];
+    long long nbins = 1;
+    for (int d = 0; d < 3; ++d) {
+        nb[d] = std::max(1, (int)std::floor(s->params.box[d] / bin_min));
+        side[d] = s->params.box[d] / nb[d];
+        nbins *= nb[d];
+    }
+    const size_t nbytes = (size_t)s->n * 3 * sizeof(double);
+    Buf tmp;
+    TRY(tmp.ensure(nbytes + (size_t)nbins * 4 + 64));
+    double *dpos = (double *)tmp.ptr;
+    int *counts = (int *)((char *)tmp.ptr + nbytes);
+    int *dnb = (int *)((char *)counts + nbins * 4);
+    double *dside = (double *)((char *)dnb + 16);
+    ljsel_status rs = dispatch(s, [&](auto z) -> ljsel_status {
+        using R = decltype(z);
+        Dev<R> S;
+        s->fill_dev(S);
+        launch_export_state(S, dpos, nullptr, 1, s->stream);
+        return LJSEL_OK;
+    });
+    if (rs != LJSEL_OK) { tmp.release(); return rs; }
+    cudaMemsetAsync(counts, 0, nbins * 4, s->stream);
+    cudaMemcpyAsync(dnb, nb, 12, cudaMemcpyHostToDevice, s->stream);
+    cudaMemcpyAsync(dside, side, 24, cudaMemcpyHostToDevice, s->stream);
+    k_bin_counts<<<div_up(s->n, 256), 256, 0, s->stream>>>(dpos, s->n, dnb, dside, counts);
+    std::vector<int> hc(nbins);
+    cudaMemcpyAsync(hc.data(), counts, nbins * 4, cudaMemcpyDeviceToHost, s->stream);
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    tmp.release();
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return LJSEL_ERR_CUDA; }
+    const double mean = (double)s->n / (double)nbins;
+    double var = 0;
+    int mx = 0;
+    long long nempty = 0;
+    for (long long b = 0; b < nbins; ++b) {
+        double d = hc[b] - mean;
+        var += d * d;
+        mx = std::max(mx, hc[b]);
+        nempty += hc[b] == 0;
+    }
+    var /= (double)nbins;
+    std::sort(hc.begin(), hc.end());
+    double median = (nbins % 2) ? hc[nbins / 2] : 0.5 * ((double)hc[nbins / 2 - 1] + (double)hc[nbins / 2]);
+    st->mean = mean;
+    st->rel_std = mean > 0 ? std::sqrt(var) / mean : 0.0;
+    st->median = median;
+    st->max = mx;
+    st->nbins = (double)nbins;
+    st->nempty = (double)nempty;
+    st->skin = s->params.skin;
+    const ljsel_config &c = s->cfg;
+    st->threads = c.method == LJSEL_METHOD_CLUSTER ? (double)s->ncl_cap * c.threads_per_unit
+                                                   : (double)s->n * std::max(1, c.threads_per_unit);
+    return LJSEL_OK;
+}
+
+ljsel_status ljsel_get_counters(ljsel_system h, ljsel_counters *c) {
+    System *s = (System *)h;
+    if (!s || !c) { set_error("NULL argument"); return LJSEL_ERR_ARG; }
+    TRY(s->read_ctrl());
+    memset(c, 0, sizeof(*c));
+    c->steps = s->h_ctrl->total_steps;
+    c->rebuilds = s->h_ctrl->rebuilds;
+    c->early_rebuilds = s->h_ctrl->early_rebuilds;
+    c->ncells = s->ncell;
+    c->capacity_retries = s->capacity_retries;
+    if (s->cfg.method == LJSEL_METHOD_VL) {
+        c->list_capacity = (int64_t)s->nl_cap * s->n;
+        c->list_entries = s->h_ctrl->need_cap;  // longest row of the last build
+    } else if (s->cfg.method == LJSEL_METHOD_CLUSTER) {
+        int ncl = 0;
+        CK(cudaMemcpy(&ncl, s->b_ncl.ptr, 4, cudaMemcpyDeviceToHost));
+        c->nclusters = ncl;
+        c->list_capacity = (int64_t)s->cp_cap * ncl;
+        c->list_entries = s->h_ctrl->need_cap;
+    }
+    return LJSEL_OK;
+}
+
+ljsel_status ljsel_default_candidates(ljsel_system h, int32_t cap, ljsel_config *out, int32_t *count) {
+    System *s = (System *)h;
+    if (!s || !count || (cap > 0 && !out)) { set_error("invalid argument"); return LJSEL_ERR_ARG; }
+    std::vector<ljsel_config> v = default_candidates(*s);
+    for (int k = 0; k < (int)v.size() && k < cap; ++k) out[k] = v[k];
+    *count = (int32_t)v.size();
+    return LJSEL_OK;
+}
+
+// One tuning phase.  Each trialled configuration is selected, its neighbour
+// structure is built (timed), then opts->trial_steps steps are advanced
+// (timed); cost per step = build time / R + step time / trial_steps, the
+// weighted average of build and force time of Sec. 2.2.5.  Trials advance
+// the simulation (Sec. 1).  Predictive strategy (Sec. 5.1): after two phases
+// a config is trialled only if its cost, extrapolated linearly from its last
+// two measurements, is within predict_factor of the best prediction, or if
+// it has not been trialled for retrial_phases phases; configs measured
+// slower than blacklist_factor x the best are dropped for good.
+ljsel_status ljsel_autotune(ljsel_system h, const ljsel_tuner_opts *opts, ljsel_config *chosen,
+                            ljsel_tuner_report *report) {
+    System *s = (System *)h;
+    if (!s || !opts) { set_error("NULL argument"); return LJSEL_ERR_ARG; }
+    if (opts->trial_steps < 1 || (opts->strategy != 0 && opts->strategy != 1)) { set_error("invalid tuner options"); return LJSEL_ERR_ARG; }
+    auto t0 = std::chrono::steady_clock::now();
+    std::vector<ljsel_config> cands;
+    if (opts->ncandidates > 0) {
+        if (!opts->candidates) { set_error("candidates is NULL"); return LJSEL_ERR_ARG; }
+        for (int k = 0; k < opts->ncandidates; ++k) {
+            TRY(validate_config(*s, &opts->candidates[k]));
+            cands.push_back(opts->candidates[k]);
+        }
+    } else {
+        cands = default_candidates(*s);
+    }
+    // (re)attach persistent per-candidate state
+    std::vector<TunerEntry *> ent;
+    for (const ljsel_config &c : cands) {
+        TunerEntry *found = nullptr;
+        for (TunerEntry &e : s->tuner)
+            if (same_cfg(e.cfg, c)) found = &e;
+        if (!found) {
+            s->tuner.push_back(TunerEntry{c, {}, -1, false});
+            found = nullptr;
+        }
+        ent.push_back(found);
+    }
+    for (size_t k = 0; k < cands.size(); ++k)
+        for (TunerEntry &e : s->tuner)
+            if (same_cfg(e.cfg, cands[k])) ent[k] = &e;
+    const int phase = s->tuner_phase;
+    // which candidates to trial
+    std::vector<char> trial(cands.size(), 1);
+    if (opts->strategy == 1 && phase >= 2) {
+        std::vector<double> pred(cands.size(), -1.0);
+        double best = 1e300;
+        for (size_t k = 0; k < cands.size(); ++k) {
+            const auto &hs = ent[k]->history;
+            if (ent[k]->blacklisted || hs.empty()) continue;
+            double p;
+            if (hs.size() == 1) p = hs.back().second;
+            else {
+                const auto &a = hs[hs.size() - 2], &b = hs[hs.size() - 1];
+                double slope = (b.second - a.second) / (double)std::max(1, b.first - a.first);
+                p = b.second + slope * (phase - b.first);
+                if (p < 0.05 * b.second) p = 0.05 * b.second;
+            }
+            pred[k] = p;
+            best = std::min(best, p);
+        }
+        for (size_t k = 0; k < cands.size(); ++k) {
+            if (ent[k]->blacklisted) { trial[k] = 0; continue; }
+            if (pred[k] < 0) { trial[k] = 1; continue; }
+            bool near = pred[k] <= opts->predict_factor * best;
+            bool stale = phase - ent[k]->last_trial_phase >= std::max(1, opts->retrial_phases);
+            trial[k] = near || stale;
+        }
+    } else {
+        for (size_t k = 0; k < cands.size(); ++k) trial[k] = !ent[k]->blacklisted;
+    }
+    std::vector<double> cost(cands.size(), -1.0);
+    int best_k = -1;
+    long long steps_total = 0;
+    for (size_t k = 0; k < cands.size(); ++k) {
+        if (!trial[k]) continue;
+        TRY(ljsel_set_config(h, &cands[k]));
+        ljsel_status st = dispatch(s, [&](auto z) -> ljsel_status {
+            using R = decltype(z);
+            // timed build
+            CK(cudaEventRecord(s->ev_a, s->stream));
+            TRY(s->ensure_structure<R>());
+            float tb = 0, ts = 0;
+            // ensure_structure synchronized the stream, so ev_b is complete
+            CK(cudaEventRecord(s->ev_b, s->stream));
+            CK(cudaEventSynchronize(s->ev_b));
+            CK(cudaEventElapsedTime(&tb, s->ev_a, s->ev_b));
+            // the build time includes one host round trip; subtract an empty one
+            CK(cudaEventRecord(s->ev_a, s->stream));
+            TRY(s->read_ctrl());
+            CK(cudaEventRecord(s->ev_b, s->stream));
+            CK(cudaEventSynchronize(s->ev_b));
+            float te = 0;
+            CK(cudaEventElapsedTime(&te, s->ev_a, s->ev_b));
+            tb = std::max(0.f, tb - te);
+            if (s->params.use_graphs && !s->gexec) TRY(s->build_graph<R>());
+            CK(cudaEventRecord(s->ev_a, s->stream));
+            TRY(s->advance<R>(opts->trial_steps));
+            CK(cudaEventRecord(s->ev_b, s->stream));
+            CK(cudaEventSynchronize(s->ev_b));
+            CK(cudaEventElapsedTime(&ts, s->ev_a, s->ev_b));
+            const int R_ = std::max(1, cands[k].rebuild_interval);
+            cost[k] = tb / R_ + ts / opts->trial_steps;
+            return LJSEL_OK;
+        });
+        if (st != LJSEL_OK) return st;
+        steps_total += opts->trial_steps;
+        ent[k]->history.push_back({phase, cost[k]});
+        if (ent[k]->history.size() > 8) ent[k]->history.erase(ent[k]->history.begin());
+        ent[k]->last_trial_phase = phase;
+        if (best_k < 0 || cost[k] < cost[best_k]) best_k = (int)k;
+    }
+    if (best_k < 0) { set_error("no candidate could be trialled"); return LJSEL_ERR_STATE; }
+    int nbl = 0, ntr = 0;
+    double overhead = 0;
+    for (size_t k = 0; k < cands.size(); ++k) {
+        if (cost[k] < 0) continue;
+        ++ntr;
+        overhead += (cost[k] - cost[best_k]) * opts->trial_steps;
+        if (opts->blacklist_factor > 0 && cost[k] > opts->blacklist_factor * cost[best_k]) ent[k]->blacklisted = true;
+    }
+    for (auto *e : ent) nbl += e->blacklisted;
+    TRY(ljsel_set_config(h, &cands[best_k]));
+    s->tuner_phase += 1;
+    auto t1 = std::chrono::steady_clock::now();
+    ljsel_tuner_report r{};
+    r.phase = s->tuner_phase;
+    r.ntrialled = ntr;
+    r.nblacklisted = nbl;
+    r.chosen_index = best_k;
+    r.chosen_cost_ms = cost[best_k];
+    r.phase_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    r.overhead_ms = overhead;
+    r.trial_steps_total = steps_total;
+    s->last_report = r;
+    if (chosen) *chosen = cands[best_k];
+    if (report) *report = r;
+    return LJSEL_OK;
+}
+
+}  // extern "C"

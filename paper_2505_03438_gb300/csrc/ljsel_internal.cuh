@@ -1,0 +1,225 @@
+// ljsel_internal.cuh -- device data layout and per-pair arithmetic shared by
+// the GPU kernels of the library (not by the CPU oracle, which is separate).
+//
+// Precision split: positions used by the pair arithmetic are a working copy
+// (float4 in the FP32 path: x, y, z and the type's bit pattern; a 32-byte
+// double quadruple in the FP64 check path); integration state (x, v) is FP64
+// structure-of-arrays; energy and virial are summed in FP64.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ljsel.h"
+
+namespace ljsel {
+
+constexpr int MAXT = LJSEL_MAX_TYPES;
+constexpr int MAXT2 = MAXT * MAXT;
+
+// A neighbour entry packs the j index (particle or cluster) into the low 27
+// bits and an image code into the top 5.  Code 0 means "no periodic image";
+// otherwise the code identifies s in {-1,0,1}^3 with x_j image = x_j + s*L.
+constexpr uint32_t JBITS = 27;
+constexpr uint32_t JMASK = (1u << JBITS) - 1u;
+
+__host__ __device__ inline uint32_t encode_image(int sx, int sy, int sz) {
+    int s = (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1);  // 13 = no image
+    return (uint32_t)((s + 14) % 27);
+}
+__host__ __device__ inline void decode_image(uint32_t c, int &sx, int &sy, int &sz) {
+    int s = ((int)c + 13) % 27;
+    sx = s % 3 - 1;
+    sy = (s / 3) % 3 - 1;
+    sz = s / 9 - 1;
+}
+
+struct __align__(32) D4 {
+    double x, y, z, w;
+};
+
+template <typename R> struct V4T;
+template <> struct V4T<float> { using type = float4; };
+template <> struct V4T<double> { using type = D4; };
+template <typename R> using V4 = typename V4T<R>::type;
+
+__device__ __forceinline__ int type_of(const float4 &p) { return __float_as_int(p.w); }
+__device__ __forceinline__ int type_of(const D4 &p) { return (int)p.w; }
+__device__ __forceinline__ float4 make_pos(float x, float y, float z, int t) { return make_float4(x, y, z, __int_as_float(t)); }
+__device__ __forceinline__ D4 make_pos(double x, double y, double z, int t) { D4 r; r.x = x; r.y = y; r.z = z; r.w = (double)t; return r; }
+__device__ __forceinline__ float4 ldpos(const float4 *p, int i) { return __ldg(p + i); }
+__device__ __forceinline__ D4 ldpos(const D4 *p, int i) { return p[i]; }
+
+// Per-type-pair constants in the working precision.  f/r = rinv2 * sr6 *
+// (e48 sr6 - e24), U = e4 sr6 (sr6 - 1) - ushift.  The cutoff test uses the
+// band [rc2lo, rc2hi] around rc2 to route borderline pairs to the exact FP64
+// predicate against rc2d (= rc*rc in double).
+template <typename R> struct PairTab {
+    R sig2[MAXT2], e24[MAXT2], e48[MAXT2], e4[MAXT2], ushift[MAXT2];
+    R rc2lo[MAXT2], rc2hi[MAXT2];
+    double rc2d[MAXT2];
+    R inv_mass_dt[MAXT];   // dt / m per type
+    double dt;
+    double half_mass[MAXT];
+    int ntypes;
+};
+
+// Device control block: flags, counters and FP64 sums, one per system.
+struct Ctrl {
+    int32_t rebuild_now;       // the rebuild kernels of this step run
+    int32_t overflow;          // a list build ran out of capacity
+    int32_t nonfinite;
+    int32_t timeout;
+    int32_t disp_exceeded;     // some particle moved >= skin/2 since the last rebuild
+    int32_t steps_since;       // steps since the last rebuild
+    int32_t pos_par;           // which working-position buffer is current
+    int32_t state_par;         // which FP64 state buffer is current
+    int32_t half_kick;         // next step kicks by dt/2 (velocities at integer time)
+    int32_t rebuild_interval;
+    int32_t loop_on;
+    int32_t pad0;
+    int64_t steps_done;        // steps done by the current advance call
+    int64_t steps_target;
+    int64_t total_steps;
+    int64_t rebuilds;
+    int64_t early_rebuilds;
+    int64_t need_cap;          // largest per-row list length required
+    int64_t list_entries;      // entries written by the last list build
+    unsigned long long npairs; // pair-export counter
+    int32_t scan_ticket;
+    int32_t pad2;
+    double epot, virial, ekin; // FP64 sums
+};
+
+// Everything a kernel needs, passed by value.
+template <typename R> struct Dev {
+    using P4 = V4<R>;
+    int n;
+    int ncell;
+    int nc[3];
+    R inv_side[3];
+    R box[3];
+    R box_lo[3];          // FP32 path: box - (float)box, for exact image shifts
+    double boxd[3];
+    int reach;            // stencil half-width in cells (1 for CSF 1, 2 for CSF 0.5)
+    R rlist2;             // squared list radius (r_c,max + skin, slightly enlarged)
+    R half_skin2;         // (skin/2)^2: displacement that forces a rebuild
+    // FP64 state, double-buffered by Ctrl::state_par; SoA [3][n]
+    double *x[2], *v[2];
+    int *id[2];           // original input index
+    int *type[2];
+    // working positions, double-buffered by Ctrl::pos_par
+    P4 *pos[2];
+    P4 *xref;             // working positions at the last rebuild
+    P4 *force;            // force buffer (N3L accumulation and compute())
+    // cells
+    int *cell_count;      // [ncell], zero between rebuilds
+    int *cell_start;      // [ncell+1]
+    int *clcell_start;    // [ncell+1] first cluster of each cell
+    int *cell_of;         // [n] cell of particle (old order at binning)
+    int *slot_of;         // [n]
+    unsigned long long *key_of;  // [n]
+    int *tmp_idx;         // [n]
+    unsigned long long *tmp_key; // [n]
+    int *cell_sorted;     // [n] cell of each sorted particle
+    int *scan_partial;    // [nblocks] decoupled look-back state
+    // Verlet lists (ELL, column-major: entry k of row i at k*stride + i)
+    uint32_t *nl;
+    int *nl_count;
+    int nl_cap;
+    int nl_stride;
+    // clusters
+    int M;                // cluster size
+    int ncl_cap;
+    int *cl_first;        // [ncl] first sorted particle
+    int *cl_count;        // [ncl]
+    int *cl_cell;         // [ncl]
+    P4 *cl_lo, *cl_hi;    // bounding boxes
+    uint32_t *cp;         // ELL cluster-pair list, column-major over i-clusters
+    int *cp_count;
+    int cp_cap;
+    int cp_stride;
+    int *ncl_total;       // device scalar: clusters of the current build
+    Ctrl *ctrl;
+    PairTab<R> tab;
+};
+
+// Image-shifted displacement x_i - (x_j + s L) in the FP32 path.  Without an
+// image it is one correctly rounded subtraction.  With an image, x_i - x_j is
+// split exactly into hi + lo (Knuth's TwoSum), s*L_hi is removed from hi
+// (exact by Sterbenz' lemma, since |x_i - x_j| is within [L/2, 2L] for any pair
+// that can be in range), and lo - s*L_lo is added: the result carries about
+// one rounding at the magnitude of the displacement, not of the box.
+__device__ __forceinline__ float image_dx(float xi, float xj, int s, float L, float Llo) {
+    float d = __fsub_rn(xi, xj);
+    if (s == 0) return d;
+    float bb = __fsub_rn(d, xi);
+    float lo = __fadd_rn(__fsub_rn(xi, __fsub_rn(d, bb)), __fsub_rn(-xj, bb));
+    float sL = s > 0 ? L : -L;
+    float sLlo = s > 0 ? Llo : -Llo;
+    float t = __fsub_rn(d, sL);
+    return __fadd_rn(t, __fsub_rn(lo, sLlo));
+}
+// FP64 path: the defining arithmetic x_i - (x_j + s L).
+__device__ __forceinline__ double image_dx(double xi, double xj, int s, double L, double) {
+    return __dsub_rn(xi, __dadd_rn(xj, (double)s * L));
+}
+
+// The exact cutoff predicate on working positions promoted to double:
+// dx = x_i - (x_j + s L), r^2 = (dx*dx + dy*dy) + dz*dz with every product
+// and sum rounded separately, in range iff r^2 < r_c^2.
+static __device__ __noinline__ bool exact_in_range(double xi, double yi, double zi, double xj, double yj, double zj,
+                                            int sx, int sy, int sz, const double *boxd, double rc2d) {
+    double dx = __dsub_rn(xi, __dadd_rn(xj, (double)sx * boxd[0]));
+    double dy = __dsub_rn(yi, __dadd_rn(yj, (double)sy * boxd[1]));
+    double dz = __dsub_rn(zi, __dadd_rn(zj, (double)sz * boxd[2]));
+    double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    return r2 < rc2d;
+}
+
+__device__ __forceinline__ float fast_rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
+
+__device__ __forceinline__ float r2_of(float dx, float dy, float dz) { return fmaf(dz, dz, fmaf(dy, dy, dx * dx)); }
+__device__ __forceinline__ double r2_of(double dx, double dy, double dz) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// Decides "r < r_c" for one pair exactly as the FP64 predicate does: in the
+// FP32 path outside a relative band of 2^-14 around r_c^2 the FP32 r^2
+// (error < 1e-6 relative) decides; inside it, the FP64 predicate.  The FP64
+// path evaluates r^2 with the defining arithmetic and decides directly.
+template <typename R> struct Cut;
+template <> struct Cut<float> {
+    __device__ __forceinline__ static bool in(float r2, float lo, float hi, const float4 &pi, const float4 &pj,
+                                              int sx, int sy, int sz, const double *boxd, double rc2d) {
+        if (r2 < lo) return true;
+        if (!(r2 <= hi)) return false;
+        return exact_in_range(pi.x, pi.y, pi.z, pj.x, pj.y, pj.z, sx, sy, sz, boxd, rc2d);
+    }
+};
+template <> struct Cut<double> {
+    __device__ __forceinline__ static bool in(double r2, double, double, const D4 &, const D4 &, int, int, int,
+                                              const double *, double rc2d) {
+        return r2 < rc2d;
+    }
+};
+
+// LJ 12-6 pair terms (Sec. 2.1): returns f/r; adds sr6*(sr6-1) to *u6 when
+// the caller accumulates energy.
+template <typename R>
+__device__ __forceinline__ R lj_fr(R r2, R sig2, R e24, R e48, R &sr6_out) {
+    R rinv2 = fast_rcp(r2);
+    R sr2 = sig2 * rinv2;
+    R sr6 = sr2 * sr2 * sr2;
+    sr6_out = sr6;
+    return (sr6 * rinv2) * (e48 * sr6 - e24);
+}
+
+inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace ljsel

@@ -1,0 +1,432 @@
+// rebuild.cu -- neighbour-structure rebuild on the GPU (Sec. 2.2.1).
+//
+// Linked cells as a counting sort: each particle is binned by its working
+// position into cells of side >= (r_c + skin) * CSF (stretched to tile the
+// box), cell counts are scanned in one decoupled look-back pass, particles
+// are scattered into their cell segments, ordered inside each cell by a
+// sub-cell Morton key (ties by input index, so the order is deterministic),
+// and the FP64 state is gathered into the new order.  Verlet lists (one
+// row per particle) and cluster-pair lists (one row per i-cluster of M
+// particles) are then built from the cells with radius r_c + skin.
+#include "kernels.cuh"
+
+namespace ljsel {
+
+namespace {
+
+constexpr int SCAN_THREADS = 512;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+constexpr unsigned long long FLAG_A = 1ull << 62;  // tile aggregate published
+constexpr unsigned long long FLAG_P = 2ull << 62;  // inclusive prefix published
+constexpr unsigned long long VAL_MASK = (1ull << 62) - 1ull;
+constexpr int SPIN_LIMIT = 1 << 22;
+
+__device__ __forceinline__ unsigned morton3(unsigned x, unsigned y, unsigned z) {
+    unsigned k = 0;
+    for (int b = 0; b < 3; ++b) k |= (((x >> b) & 1u) << (3 * b)) | (((y >> b) & 1u) << (3 * b + 1)) | (((z >> b) & 1u) << (3 * b + 2));
+    return k;
+}
+
+__device__ __forceinline__ int floor_div(int a, int b) { int q = a / b; return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q; }
+
+template <typename R>
+__global__ void k_bin(Dev<R> S, int ntiles) {
+    Ctrl *C = S.ctrl;
+    if (!C->rebuild_now) return;
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < ntiles) reinterpret_cast<unsigned long long *>(S.scan_partial)[p] = 0ull;
+    if (p == 0) C->need_cap = 0;
+    if (p >= S.n) return;
+    const int sp = C->state_par;
+    double *X = S.x[sp];
+    int c3[3];
+    unsigned sub[3];
+    bool bad = false;
+    for (int d = 0; d < 3; ++d) {
+        double L = S.boxd[d];
+        double xd = X[d * S.n + p];
+        if (!(xd == xd) || fabs(xd) > 4.0 * L) { bad = true; xd = 0.0; }
+        if (xd < 0.0) xd += L;
+        if (xd >= L) xd -= L;
+        if (xd < 0.0 || xd >= L) { xd = xd - L * floor(xd / L); if (xd >= L) xd = 0.0; }
+        X[d * S.n + p] = xd;
+        R w = (R)xd;
+        R f = w * S.inv_side[d];
+        int c = (int)floor(f);
+        c = c < 0 ? 0 : (c > S.nc[d] - 1 ? S.nc[d] - 1 : c);
+        int s = (int)((f - (R)c) * (R)8);
+        sub[d] = (unsigned)(s < 0 ? 0 : (s > 7 ? 7 : s));
+        c3[d] = c;
+    }
+    if (bad) C->nonfinite = 1;
+    int cell = (c3[2] * S.nc[1] + c3[1]) * S.nc[0] + c3[0];
+    S.cell_of[p] = cell;
+    S.slot_of[p] = atomicAdd(&S.cell_count[cell], 1);
+    S.key_of[p] = ((unsigned long long)morton3(sub[0], sub[1], sub[2]) << 32) | (unsigned)S.id[sp][p];
+}
+
+__device__ __forceinline__ unsigned long long warp_incl_scan(unsigned long long v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Exclusive scan of (count, ceil(count / M)) packed as hi/lo 31-bit fields of
+// one 64-bit word.  Tiles take tickets in launch order, publish their
+// aggregate, then look back over predecessors (which hold earlier tickets and
+// so are running or done); every wait is bounded and sets Ctrl::timeout.
+template <typename R>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan(Dev<R> S, int M, int ntiles) {
+    Ctrl *C = S.ctrl;
+    if (!C->rebuild_now) return;
+    __shared__ int s_tile;
+    __shared__ unsigned long long s_warp[SCAN_THREADS / 32];
+    __shared__ unsigned long long s_excl;
+    if (threadIdx.x == 0) {
+        int t = atomicAdd(&C->scan_ticket, 1);
+        if (t == ntiles - 1) C->scan_ticket = 0;
+        s_tile = t;
+    }
+    __syncthreads();
+    const int tile = s_tile;
+    const int base = tile * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    unsigned long long item[SCAN_ITEMS];
+    unsigned long long run = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        int c = base + k;
+        int cnt = c < S.ncell ? S.cell_count[c] : 0;
+        unsigned long long v = ((unsigned long long)cnt << 31) | (unsigned long long)((cnt + M - 1) / M);
+        item[k] = run;
+        run += v;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long incl = warp_incl_scan(run);
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long w = lane < SCAN_THREADS / 32 ? s_warp[lane] : 0ull;
+        unsigned long long wi = warp_incl_scan(w);
+        if (lane < SCAN_THREADS / 32) s_warp[lane] = wi - w;  // exclusive per warp
+        if (lane == SCAN_THREADS / 32 - 1) {
+            unsigned long long agg = wi;
+            volatile unsigned long long *st = reinterpret_cast<volatile unsigned long long *>(S.scan_partial);
+            unsigned long long excl = 0;
+            if (tile == 0) {
+                __threadfence();
+                atomicExch(reinterpret_cast<unsigned long long *>(S.scan_partial), FLAG_P | agg);
+            } else {
+                __threadfence();
+                atomicExch(reinterpret_cast<unsigned long long *>(S.scan_partial) + tile, FLAG_A | agg);
+                int p = tile - 1;
+                while (p >= 0) {
+                    unsigned long long v = 0;
+                    int it = 0;
+                    while (true) {
+                        v = st[p];
+                        if (v & (FLAG_A | FLAG_P)) break;
+                        if (++it > SPIN_LIMIT) break;
+                        __nanosleep(32);
+                    }
+                    if (!(v & (FLAG_A | FLAG_P))) { C->timeout = 1; break; }
+                    excl += v & VAL_MASK;
+                    if (v & FLAG_P) break;
+                    --p;
+                }
+                __threadfence();
+                atomicExch(reinterpret_cast<unsigned long long *>(S.scan_partial) + tile, FLAG_P | ((excl + agg) & VAL_MASK));
+            }
+            s_excl = excl;
+            if (tile == ntiles - 1) {
+                unsigned long long tot = excl + agg;
+                S.cell_start[S.ncell] = (int)(tot >> 31);
+                S.clcell_start[S.ncell] = (int)(tot & 0x7fffffffull);
+                *S.ncl_total = (int)(tot & 0x7fffffffull);
+            }
+        }
+    }
+    __syncthreads();
+    const unsigned long long off = s_excl + s_warp[warp] + (incl - run);
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        int c = base + k;
+        if (c < S.ncell) {
+            unsigned long long v = off + item[k];
+            S.cell_start[c] = (int)(v >> 31);
+            S.clcell_start[c] = (int)(v & 0x7fffffffull);
+            S.cell_count[c] = 0;
+        }
+    }
+}
+
+template <typename R>
+__global__ void k_scatter(Dev<R> S) {
+    Ctrl *C = S.ctrl;
+    if (!C->rebuild_now) return;
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= S.n) return;
+    int dst = S.cell_start[S.cell_of[p]] + S.slot_of[p];
+    S.tmp_idx[dst] = p;
+    S.tmp_key[dst] = S.key_of[p];
+}
+
+template <typename R>
+__device__ __forceinline__ void gather_one(const Dev<R> &S, int sp, int pp, int q, int p, int cell) {
+    const int n = S.n;
+    const double *X = S.x[sp];
+    const double *V = S.v[sp];
+    double *Xn = S.x[sp ^ 1];
+    double *Vn = S.v[sp ^ 1];
+    double x0 = X[p], x1 = X[n + p], x2 = X[2 * n + p];
+    Xn[q] = x0; Xn[n + q] = x1; Xn[2 * n + q] = x2;
+    Vn[q] = V[p]; Vn[n + q] = V[n + p]; Vn[2 * n + q] = V[2 * n + p];
+    S.id[sp ^ 1][q] = S.id[sp][p];
+    int t = S.type[sp][p];
+    S.type[sp ^ 1][q] = t;
+    V4<R> w = make_pos((R)x0, (R)x1, (R)x2, t);
+    S.pos[pp][q] = w;
+    S.xref[q] = w;
+    S.cell_sorted[q] = cell;
+}
+
+// One warp per cell: rank each element of the cell segment by its key and
+// gather the particle state into its final slot.
+template <typename R>
+__global__ void k_sortgather(Dev<R> S) {
+    Ctrl *C = S.ctrl;
+    if (!C->rebuild_now) return;
+    const int lane = threadIdx.x & 31;
+    const int cell = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (cell >= S.ncell) return;
+    const int sp = C->state_par, pp = C->pos_par;
+    const int start = S.cell_start[cell];
+    const int m = S.cell_start[cell + 1] - start;
+    if (m <= 32) {
+        unsigned long long key = lane < m ? S.tmp_key[start + lane] : ~0ull;
+        int rank = 0;
+        for (int t = 0; t < m; ++t) rank += (__shfl_sync(0xffffffffu, key, t) < key) ? 1 : 0;
+        if (lane < m) gather_one(S, sp, pp, start + rank, S.tmp_idx[start + lane], cell);
+    } else {
+        for (int e = lane; e < m; e += 32) {
+            unsigned long long key = S.tmp_key[start + e];
+            int rank = 0;
+            for (int f = 0; f < m; ++f) rank += (S.tmp_key[start + f] < key) ? 1 : 0;
+            gather_one(S, sp, pp, start + rank, S.tmp_idx[start + e], cell);
+        }
+    }
+}
+
+// Verlet-list row of particle i (sorted index): all j in the stencil cells
+// with r^2 < r_list^2 (working precision), j != i; with N3L only j > i.
+template <typename R, bool N3L>
+__global__ void k_vl_build(Dev<R> S) {
+    Ctrl *C = S.ctrl;
+    if (!C->rebuild_now) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S.n) return;
+    const int pp = C->pos_par;
+    const V4<R> *P = S.pos[pp];
+    const V4<R> pi = P[i];
+    const int c = S.cell_sorted[i];
+    const int cx = c % S.nc[0], cy = (c / S.nc[0]) % S.nc[1], cz = c / (S.nc[0] * S.nc[1]);
+    int cnt = 0;
+    const int rch = S.reach;
+    for (int oz = -rch; oz <= rch; ++oz) {
+        int rz = cz + oz, sz = floor_div(rz, S.nc[2]);
+        if (sz < -1 || sz > 1) continue;
+        int wz = rz - sz * S.nc[2];
+        for (int oy = -rch; oy <= rch; ++oy) {
+            int ry = cy + oy, sy = floor_div(ry, S.nc[1]);
+            if (sy < -1 || sy > 1) continue;
+            int wy = ry - sy * S.nc[1];
+            for (int ox = -rch; ox <= rch; ++ox) {
+                int rx = cx + ox, sx = floor_div(rx, S.nc[0]);
+                if (sx < -1 || sx > 1) continue;
+                int wx = rx - sx * S.nc[0];
+                int cc = (wz * S.nc[1] + wy) * S.nc[0] + wx;
+                uint32_t code = encode_image(sx, sy, sz);
+                int jb = S.cell_start[cc], je = S.cell_start[cc + 1];
+                for (int j = jb; j < je; ++j) {
+                    if (j == i && code == 0) continue;
+                    if (N3L && j < i) continue;
+                    V4<R> pj = P[j];
+                    R dx = image_dx(pi.x, pj.x, sx, S.box[0], S.box_lo[0]);
+                    R dy = image_dx(pi.y, pj.y, sy, S.box[1], S.box_lo[1]);
+                    R dz = image_dx(pi.z, pj.z, sz, S.box[2], S.box_lo[2]);
+                    R r2 = r2_of(dx, dy, dz);
+                    if (r2 < S.rlist2) {
+                        if (cnt < S.nl_cap) S.nl[(size_t)cnt * S.nl_stride + i] = (uint32_t)j | (code << JBITS);
+                        ++cnt;
+                    }
+                }
+            }
+        }
+    }
+    S.nl_count[i] = cnt < S.nl_cap ? cnt : S.nl_cap;
+    if (cnt > S.nl_cap) C->overflow = 1;
+    atomicMax(reinterpret_cast<unsigned long long *>(&C->need_cap), (unsigned long long)cnt);
+}
+
+// Clusters: each cell's segment is cut into chunks of M consecutive sorted
+// particles (the last may be shorter); one thread per cell writes its
+// clusters' extent and bounding box.
+template <typename R>
+__global__ void k_cluster_form(Dev<R> S) {
+    Ctrl *C = S.ctrl;
+    if (!C->rebuild_now) return;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= S.ncell) return;
+    const V4<R> *P = S.pos[C->pos_par];
+    const int start = S.cell_start[c], m = S.cell_start[c + 1] - start;
+    const int cl0 = S.clcell_start[c];
+    for (int k = 0; k * S.M < m; ++k) {
+        int cl = cl0 + k;
+        if (cl >= S.ncl_cap) { C->overflow = 1; return; }
+        int first = start + k * S.M;
+        int cnt = min(S.M, m - k * S.M);
+        V4<R> lo = P[first], hi = lo;
+        for (int a = 1; a < cnt; ++a) {
+            V4<R> q = P[first + a];
+            lo.x = min(lo.x, q.x); lo.y = min(lo.y, q.y); lo.z = min(lo.z, q.z);
+            hi.x = max(hi.x, q.x); hi.y = max(hi.y, q.y); hi.z = max(hi.z, q.z);
+        }
+        S.cl_first[cl] = first;
+        S.cl_count[cl] = cnt;
+        S.cl_cell[cl] = c;
+        S.cl_lo[cl] = lo;
+        S.cl_hi[cl] = hi;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ R box_gap(R loi, R hii, R loj, R hij, int s, R L) {
+    R sh = s == 0 ? (R)0 : (s > 0 ? L : -L);
+    R a = (loj + sh) - hii;
+    R b = loi - (hij + sh);
+    R g = a > b ? a : b;
+    return g > (R)0 ? g : (R)0;
+}
+
+// Cluster-pair list row of i-cluster ci: j-clusters in the stencil cells
+// whose bounding boxes come closer than r_list and (M <= 8) that hold at
+// least one particle pair closer than r_list.  With N3L only cj > ci and the
+// cluster itself.
+template <typename R, bool N3L>
+__global__ void k_cp_build(Dev<R> S) {
+    Ctrl *C = S.ctrl;
+    if (!C->rebuild_now) return;
+    const int ci = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ncl = *S.ncl_total;
+    if (ci >= ncl || ci >= S.ncl_cap) return;
+    const V4<R> *P = S.pos[C->pos_par];
+    const V4<R> loi = S.cl_lo[ci], hii = S.cl_hi[ci];
+    const int fi = S.cl_first[ci], ni = S.cl_count[ci];
+    const int c = S.cl_cell[ci];
+    const int cx = c % S.nc[0], cy = (c / S.nc[0]) % S.nc[1], cz = c / (S.nc[0] * S.nc[1]);
+    const int rch = S.reach;
+    int cnt = 0;
+    for (int oz = -rch; oz <= rch; ++oz) {
+        int rz = cz + oz, sz = floor_div(rz, S.nc[2]);
+        if (sz < -1 || sz > 1) continue;
+        int wz = rz - sz * S.nc[2];
+        for (int oy = -rch; oy <= rch; ++oy) {
+            int ry = cy + oy, sy = floor_div(ry, S.nc[1]);
+            if (sy < -1 || sy > 1) continue;
+            int wy = ry - sy * S.nc[1];
+            for (int ox = -rch; ox <= rch; ++ox) {
+                int rx = cx + ox, sx = floor_div(rx, S.nc[0]);
+                if (sx < -1 || sx > 1) continue;
+                int wx = rx - sx * S.nc[0];
+                int cc = (wz * S.nc[1] + wy) * S.nc[0] + wx;
+                uint32_t code = encode_image(sx, sy, sz);
+                int jb = S.clcell_start[cc], je = S.clcell_start[cc + 1];
+                for (int cj = jb; cj < je; ++cj) {
+                    if (N3L && (cj < ci || (cj == ci && code != 0))) continue;
+                    V4<R> loj = S.cl_lo[cj], hij = S.cl_hi[cj];
+                    R gx = box_gap(loi.x, hii.x, loj.x, hij.x, sx, S.box[0]);
+                    R gy = box_gap(loi.y, hii.y, loj.y, hij.y, sy, S.box[1]);
+                    R gz = box_gap(loi.z, hii.z, loj.z, hij.z, sz, S.box[2]);
+                    if (!(gx * gx + gy * gy + gz * gz < S.rlist2)) continue;
+                    bool keep = S.M > 8;
+                    if (!keep) {
+                        const int fj = S.cl_first[cj], nj = S.cl_count[cj];
+                        for (int a = 0; a < ni && !keep; ++a) {
+                            V4<R> pa = P[fi + a];
+                            for (int b = 0; b < nj; ++b) {
+                                if (cj == ci && code == 0 && a == b) continue;
+                                V4<R> pb = P[fj + b];
+                                R dx = image_dx(pa.x, pb.x, sx, S.box[0], S.box_lo[0]);
+                                R dy = image_dx(pa.y, pb.y, sy, S.box[1], S.box_lo[1]);
+                                R dz = image_dx(pa.z, pb.z, sz, S.box[2], S.box_lo[2]);
+                                if (r2_of(dx, dy, dz) < S.rlist2) { keep = true; break; }
+                            }
+                        }
+                    }
+                    if (!keep) continue;
+                    if (cnt < S.cp_cap) S.cp[(size_t)cnt * S.cp_stride + ci] = (uint32_t)cj | (code << JBITS);
+                    ++cnt;
+                }
+            }
+        }
+    }
+    S.cp_count[ci] = cnt < S.cp_cap ? cnt : S.cp_cap;
+    if (cnt > S.cp_cap) C->overflow = 1;
+    atomicMax(reinterpret_cast<unsigned long long *>(&C->need_cap), (unsigned long long)cnt);
+}
+
+__global__ void k_rebuild_finish(Ctrl *C) {
+    if (!C->rebuild_now) return;
+    C->state_par ^= 1;
+    C->steps_since = 0;
+    C->rebuilds += 1;
+    C->rebuild_now = 0;
+}
+
+}  // namespace
+
+template <typename R> void launch_bin(const Dev<R> &S, cudaStream_t st) {
+    int ntiles = div_up(S.ncell, SCAN_TILE);
+    int n = S.n > ntiles ? S.n : ntiles;
+    k_bin<R><<<div_up(n, 256), 256, 0, st>>>(S, ntiles);
+}
+template <typename R> void launch_scan(const Dev<R> &S, int M, cudaStream_t st) {
+    int ntiles = div_up(S.ncell, SCAN_TILE);
+    k_scan<R><<<ntiles, SCAN_THREADS, 0, st>>>(S, M < 1 ? 1 : M, ntiles);
+}
+template <typename R> void launch_scatter(const Dev<R> &S, cudaStream_t st) {
+    k_scatter<R><<<div_up(S.n, 256), 256, 0, st>>>(S);
+}
+template <typename R> void launch_sortgather(const Dev<R> &S, cudaStream_t st) {
+    k_sortgather<R><<<div_up((long long)S.ncell * 32, 256), 256, 0, st>>>(S);
+}
+template <typename R> void launch_vl_build(const Dev<R> &S, bool n3l, cudaStream_t st) {
+    if (n3l) k_vl_build<R, true><<<div_up(S.n, 128), 128, 0, st>>>(S);
+    else k_vl_build<R, false><<<div_up(S.n, 128), 128, 0, st>>>(S);
+}
+template <typename R> void launch_cluster_form(const Dev<R> &S, cudaStream_t st) {
+    k_cluster_form<R><<<div_up(S.ncell, 128), 128, 0, st>>>(S);
+}
+template <typename R> void launch_cp_build(const Dev<R> &S, bool n3l, cudaStream_t st) {
+    if (n3l) k_cp_build<R, true><<<div_up(S.ncl_cap, 128), 128, 0, st>>>(S);
+    else k_cp_build<R, false><<<div_up(S.ncl_cap, 128), 128, 0, st>>>(S);
+}
+void launch_rebuild_finish(Ctrl *C, cudaStream_t st) { k_rebuild_finish<<<1, 1, 0, st>>>(C); }
+
+#define INST(R)                                                                 \
+    template void launch_bin<R>(const Dev<R> &, cudaStream_t);                  \
+    template void launch_scan<R>(const Dev<R> &, int, cudaStream_t);            \
+    template void launch_scatter<R>(const Dev<R> &, cudaStream_t);              \
+    template void launch_sortgather<R>(const Dev<R> &, cudaStream_t);           \
+    template void launch_vl_build<R>(const Dev<R> &, bool, cudaStream_t);       \
+    template void launch_cluster_form<R>(const Dev<R> &, cudaStream_t);         \
+    template void launch_cp_build<R>(const Dev<R> &, bool, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace ljsel

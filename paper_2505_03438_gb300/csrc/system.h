@@ -1,0 +1,95 @@
+// system.h -- host-side state of one particle system (behind ljsel_system).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "ljsel_internal.cuh"
+
+namespace ljsel {
+
+void set_error(const std::string &m);
+const char *last_error();
+
+struct Buf {
+    void *ptr = nullptr;
+    size_t size = 0;
+    ljsel_status ensure(size_t bytes);
+    void release();
+};
+
+ljsel_status validate_params(const ljsel_params *p);
+
+// Per-configuration memory of the predictive tuning strategy (Sec. 5.1).
+struct TunerEntry {
+    ljsel_config cfg;
+    std::vector<std::pair<int, double>> history;  // (phase, cost ms/step)
+    int last_trial_phase = -1;
+    bool blacklisted = false;
+};
+
+struct System {
+    ljsel_params params{};
+    int n = 0;
+    int precision = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+    ljsel_config cfg{};
+    // grid
+    int nc[3] = {1, 1, 1};
+    double side[3] = {1, 1, 1};
+    int ncell = 1;
+    int reach = 1;
+    double rlist = 0;
+    int M = 1;
+    // list capacities
+    int nl_cap = 0, nl_stride = 0;
+    int ncl_cap = 0, cp_cap = 0, cp_stride = 0;
+    long long capacity_retries = 0;
+    bool structure_dirty = true;
+    bool synced = true;  // velocities at the integer step
+    // device buffers
+    Buf b_x[2], b_v[2], b_id[2], b_type[2], b_pos[2];
+    Buf b_xref, b_force;
+    Buf b_cell_count, b_cell_start, b_clcell_start, b_cell_of, b_slot_of, b_key_of, b_tmp_idx, b_tmp_key,
+        b_cell_sorted, b_scan;
+    Buf b_nl, b_nl_count;
+    Buf b_cl_first, b_cl_count, b_cl_cell, b_cl_lo, b_cl_hi, b_cp, b_cp_count, b_ncl;
+    Buf b_ctrl, b_io;
+    Ctrl *h_ctrl = nullptr;  // pinned mirror
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+    // graph of the stepping loop for the current configuration
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    // tuner state
+    std::vector<TunerEntry> tuner;
+    int tuner_phase = 0;
+    ljsel_tuner_report last_report{};
+
+    ~System();
+    std::vector<Buf *> all_bufs();
+    void drop_graph();
+    size_t p4() const;
+    void plan_grid();
+    ljsel_status alloc_base();
+    ljsel_status apply_config();
+    ljsel_status cmd(int op, long long a);
+    ljsel_status read_ctrl();
+    ljsel_status check_device_errors();
+    ljsel_status handle_overflow();
+    template <typename R> void fill_dev(Dev<R> &S) const;
+    template <typename R> void enqueue_rebuild(const Dev<R> &S, cudaStream_t st);
+    template <typename R> void enqueue_step(const Dev<R> &S, bool ev, cudaStream_t st);
+    template <typename R> ljsel_status ensure_structure();
+    template <typename R> ljsel_status build_graph();
+    template <typename R> ljsel_status advance(long long nsteps);
+    template <typename R> ljsel_status compute_forces(bool ev);
+    template <typename R> ljsel_status sync_velocities();
+};
+
+ljsel_status validate_config(const System &s, const ljsel_config *c);
+
+enum { CMD_REBUILD = 1, CMD_BEGIN = 2, CMD_RESET_EV = 3, CMD_RESET_PAIRS = 4, CMD_HALF_KICK = 5, CMD_CLEAR = 6,
+       CMD_INTERVAL = 7 };
+
+}  // namespace ljsel

@@ -1,0 +1,271 @@
+"""GPU path against the FP64 oracle, through the C ABI.
+
+Bars: the within-cutoff pair set is bit-exact (the oracle evaluates the exact
+FP64 predicate on the working positions the GPU used); FP32 forces are within
+1e-5 relative RMS of the oracle's FP64 forces on those positions; energy and
+virial within 2e-6 relative (FP32 pair terms summed in FP64); the FP64 check
+path matches the oracle to 1e-12.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_03438_gb300 import scenarios
+
+pytestmark = pytest.mark.gpu
+
+FORCE_TOL = 1e-5
+SUM_TOL = 2e-6
+
+
+@pytest.fixture(scope="module")
+def lj():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2505_03438_gb300 as m
+    return m
+
+
+CONFIGS = [
+    dict(method="LC", newton3=False, csf=1.0),
+    dict(method="LC", newton3=True, csf=1.0),
+    dict(method="LC", newton3=False, csf=0.5),
+    dict(method="LC", newton3=True, csf=0.5),
+    dict(method="VL", newton3=False, threads_per_unit=1),
+    dict(method="VL", newton3=False, threads_per_unit=4),
+    dict(method="VL", newton3=True, threads_per_unit=1),
+    dict(method="VL", newton3=True, threads_per_unit=4),
+    dict(method="CL", cluster_size=4, newton3=False, threads_per_unit=4),
+    dict(method="CL", cluster_size=4, newton3=False, threads_per_unit=16),
+    dict(method="CL", cluster_size=4, newton3=True, threads_per_unit=4),
+    dict(method="CL", cluster_size=8, newton3=False, threads_per_unit=8),
+    dict(method="CL", cluster_size=8, newton3=False, threads_per_unit=32),
+    dict(method="CL", cluster_size=8, newton3=True, threads_per_unit=8),
+    dict(method="CL", cluster_size=32, newton3=False, threads_per_unit=32),
+    dict(method="CL", cluster_size=32, newton3=True, threads_per_unit=32),
+]
+
+
+def cfg_id(c):
+    return "%s%s-%s-t%d-csf%g" % (c["method"], c.get("cluster_size", ""), "n3" if c["newton3"] else "full",
+                                 c.get("threads_per_unit", 1), c.get("csf", 1.0))
+
+
+def _systems():
+    out = {
+        "jfcc864": scenarios.fcc_liquid(6, seed=11, jitter=0.15),
+        "gas500": scenarios.random_gas(500, 12.0, seed=12, min_dist=0.8),
+        "tinybox": scenarios.random_gas(150, 5.75, seed=13, min_dist=0.8),
+        "binary": scenarios.binary_mixture(seed=14, nside=12),
+    }
+    return out
+
+
+SYSTEMS = _systems()
+
+
+def _orc_params(sc):
+    return oracle.make_params(sc["box"], sc["eps"], sc["sigma"], sc["rcut"], sc.get("shift", True))
+
+
+def check_against_oracle(sys_, sc, force_tol=FORCE_TOL, sum_tol=SUM_TOL):
+    F, e, w = sys_.compute()
+    xw = sys_.work_positions()
+    ref = oracle.forces_cells(xw, sc["types"], _orc_params(sc), pairs=True)
+    pairs, cnt = sys_.pairs()
+    assert cnt == ref["count"], (cnt, ref["count"])
+    assert np.array_equal(oracle.sorted_pairs(pairs), oracle.sorted_pairs(ref["pairs"]))
+    rel = np.linalg.norm(F - ref["F"]) / np.linalg.norm(ref["F"])
+    assert rel <= force_tol, rel
+    assert abs(e - ref["U"]) <= sum_tol * max(abs(ref["U"]), 1.0), (e, ref["U"])
+    assert abs(w - ref["W"]) <= sum_tol * max(abs(ref["W"]), 1.0), (w, ref["W"])
+    return rel
+
+
+@pytest.mark.parametrize("cfg", CONFIGS, ids=cfg_id)
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_pairs_forces_fp32(lj, cfg, name):
+    sc = SYSTEMS[name]
+    s = lj.System(sc)
+    s.set_config(rebuild_interval=10, **cfg)
+    check_against_oracle(s, sc)
+    # after 30 steps the positions have drifted (not wrapped) and the lists are reused
+    s.step(30)
+    check_against_oracle(s, sc)
+    s.close()
+
+
+@pytest.mark.parametrize("cfg", CONFIGS, ids=cfg_id)
+def test_pairs_forces_fp64(lj, cfg):
+    for name in ("jfcc864", "binary"):
+        sc = SYSTEMS[name]
+        s = lj.System(sc, precision=1)
+        s.set_config(rebuild_interval=10, **cfg)
+        check_against_oracle(s, sc, force_tol=1e-12, sum_tol=1e-12)
+        s.step(15)
+        check_against_oracle(s, sc, force_tol=1e-12, sum_tol=1e-12)
+        s.close()
+
+
+def _wrapdiff(a, b, L):
+    d = a - b
+    return d - L * np.round(d / L)
+
+
+def test_fp64_trajectory_small_fcc(lj):
+    """Plain method in FP64: N = 4000 fcc, linked cells of side >= r_c, 100 NVE
+    steps; the GPU trajectory equals the oracle's up to rounding."""
+    sc = scenarios.small_fcc()
+    s = lj.System(sc, precision=1)
+    s.set_config(method="LC", newton3=False, rebuild_interval=1, csf=1.0)
+    ep0, ek0, _ = s.energy()
+    s.step(sc["nsteps"])
+    x, v = s.state()
+    ep1, ek1, _ = s.energy()
+    xo, vo, epo, eko, _ = oracle.verlet_run(sc["x"], sc["v"], None, [1.0], _orc_params(sc), sc["dt"], sc["nsteps"])
+    L = sc["box"][0]
+    assert np.abs(_wrapdiff(x, xo, L)).max() < 1e-10
+    assert np.abs(v - vo).max() < 1e-10
+    assert abs(ep0 - epo[0]) < 1e-10 * abs(epo[0]) and abs(ek0 - eko[0]) < 1e-10 * abs(eko[0])
+    assert abs(ep1 - epo[-1]) < 1e-9 * abs(epo[-1]) and abs(ek1 - eko[-1]) < 1e-9 * abs(eko[-1])
+    s.close()
+
+
+@pytest.mark.parametrize("method", ["VL", "LC", "CL"])
+def test_fp32_trajectory_tracks_fp64(lj, method):
+    sc = scenarios.fcc_liquid(8, seed=21, jitter=0.05)
+    s = lj.System(sc)
+    kw = dict(method=method, rebuild_interval=10)
+    if method == "CL":
+        kw.update(cluster_size=8, threads_per_unit=8)
+    s.set_config(**kw)
+    e0 = sum(s.energy()[:2])
+    s.step(100)
+    x, v = s.state()
+    e1 = sum(s.energy()[:2])
+    xo, vo, epo, eko, _ = oracle.verlet_run(sc["x"], sc["v"], None, [1.0], _orc_params(sc), sc["dt"], 100)
+    L = sc["box"][0]
+    assert abs(e1 - e0) < 1e-3 * abs(e0)
+    assert abs(e1 - (epo[-1] + eko[-1])) < 1e-4 * abs(e0)
+    assert np.abs(_wrapdiff(x, xo, L)).max() < 1e-3
+    s.close()
+
+
+def test_graph_equals_eager(lj):
+    sc = scenarios.fcc_liquid(6, seed=31, jitter=0.1)
+    out = []
+    for g in (True, False):
+        s = lj.System(sc, use_graphs=g)
+        s.set_config(method="VL", rebuild_interval=7)
+        s.step(45)
+        out.append(s.state())
+        c = s.counters()
+        assert c["steps"] == 45
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_displacement_forces_early_rebuild(lj):
+    # hot gas: particles cross skin/2 long before R = 200 steps
+    sc = scenarios.random_gas(800, 14.0, seed=41, min_dist=0.9, temperature=6.0)
+    s = lj.System(sc, skin=0.2)
+    s.set_config(method="VL", rebuild_interval=200)
+    s.step(120)
+    c = s.counters()
+    assert c["early_rebuilds"] >= 2, c
+    check_against_oracle(s, sc)
+    s.close()
+
+
+def test_capacity_overflow_is_recovered(lj):
+    # a dense droplet in a large sparse box: the mean-density estimate of the
+    # list length is far too small, the first build overflows and is redone
+    rng = np.random.default_rng(5)
+    core = scenarios.fcc_lattice(5, 0.9)[0]
+    core = core - core.mean(0) + 15.0
+    gas = rng.uniform(0, 30.0, (300, 3))
+    x = np.concatenate([core, gas])
+    keep = np.ones(len(x), bool)
+    for k in range(len(core), len(x)):
+        d = np.abs(x[:k][keep[:k]] - x[k])
+        d = np.minimum(d, 30.0 - d)
+        if ((d * d).sum(1) < 0.81).any():
+            keep[k] = False
+    x = x[keep]
+    v = scenarios.maxwell_boltzmann(len(x), 1.0, 1.0, rng)
+    sc = dict(x=x, v=v, types=np.zeros(len(x), np.int32), box=np.full(3, 30.0), eps=np.ones((1, 1)),
+              sigma=np.ones((1, 1)), rcut=np.full((1, 1), 2.5), mass=np.ones(1), skin=0.3, dt=0.005, shift=True)
+    for cfg in (dict(method="VL"), dict(method="CL", cluster_size=8, threads_per_unit=8)):
+        s = lj.System(sc)
+        s.set_config(**cfg)
+        check_against_oracle(s, sc)
+        assert s.counters()["capacity_retries"] >= 1
+        s.step(20)
+        check_against_oracle(s, sc)
+        s.close()
+
+
+def test_live_statistics(lj):
+    for sc in (scenarios.fcc_liquid(7, seed=51, jitter=0.2), scenarios.random_gas(400, 14.0, seed=52, min_dist=0.8)):
+        s = lj.System(sc)
+        s.step(10)
+        st = s.stats()
+        x, _ = s.state()
+        ref = oracle.bin_stats(x, sc["box"], 2.5 + sc["skin"])
+        for k in ("mean", "rel_std", "median", "max", "nbins", "nempty"):
+            assert abs(st[k] - ref[k]) <= 1e-12 * max(1.0, abs(ref[k])), (k, st[k], ref[k])
+        s.close()
+
+
+def test_autotune_full_and_predictive(lj):
+    sc = scenarios.fcc_liquid(8, seed=61, jitter=0.1)
+    s = lj.System(sc)
+    cands = lj.ljsel_default_candidates(s.h)
+    assert len(cands) >= 15
+    chosen, rep = s.autotune(strategy=0, trial_steps=10)
+    assert rep["ntrialled"] == len(cands) and rep["chosen_cost_ms"] > 0
+    assert any(chosen.name() == c.name() for c in cands)
+    assert s.config().name() == chosen.name()
+    assert s.counters()["steps"] == 10 * len(cands)
+    check_against_oracle(s, sc)
+    # predictive strategy: two full phases, then a filtered one
+    s2 = lj.System(sc)
+    for ph in range(3):
+        _, rep = s2.autotune(strategy=1, trial_steps=10, blacklist_factor=10.0)
+    assert rep["ntrialled"] < len(cands)
+    check_against_oracle(s2, sc)
+    s.close()
+    s2.close()
+
+
+def test_device_pointer_inputs(lj):
+    import torch
+    sc = scenarios.fcc_liquid(5, seed=71, jitter=0.1)
+    x = torch.tensor(sc["x"], device="cuda")
+    v = torch.tensor(sc["v"], device="cuda")
+    t = torch.zeros(len(sc["x"]), dtype=torch.int32, device="cuda")
+    p = lj.make_params(sc["box"], skin=0.3)
+    h = lj.ljsel_create(p, len(sc["x"]), x, v, t, torch.cuda.current_stream().cuda_stream)
+    F = torch.zeros_like(x)
+    e, w = lj.ljsel_compute(h, F)
+    torch.cuda.synchronize()
+    xw = np.zeros_like(sc["x"])
+    lj.ljsel_get_work_positions(h, xw)
+    ref = oracle.forces_cells(xw, None, _orc_params(sc))
+    Fh = F.cpu().numpy()
+    assert np.linalg.norm(Fh - ref["F"]) / np.linalg.norm(ref["F"]) < FORCE_TOL
+    lj.ljsel_destroy(h)
+
+
+def test_liquid_1m_full_size(lj):
+    """Full-size homogeneous liquid (N = 1,048,576) in the benchmark's launch
+    configuration: whole pair set and all forces against the oracle."""
+    sc = scenarios.liquid_1m()
+    s = lj.System(sc)
+    s.set_config(method="VL", rebuild_interval=10)
+    s.step(20)
+    check_against_oracle(s, sc)
+    s.close()
