@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Benchmark: LJ particle-steps/s on the homogeneous 1M-atom liquid, the
+auto-tuned GPU path against every fixed configuration, with the roofline
+fraction of the dominant kernel.
+
+Workload (synthetic; the paper's md-flexible inputs are not available):
+N = 1,048,576 LJ particles on a 64^3 x 4 fcc lattice, density 0.8442,
+Maxwell-Boltzmann velocities at T = 0.72 (seed 2), cutoff 2.5 sigma with an
+energy shift, skin 0.3 sigma, rebuild every 10 steps (or earlier when a
+particle moves skin/2), dt 0.005, 1000 steps per run, FP32 pair arithmetic
+with FP64 integration and sums.
+
+A "step" is one Stormer-Verlet step of the whole system (binning, lists,
+forces, update).  The timed region of the default run holds one Full Search
+tuning phase (its trial steps advance the simulation and count as steps)
+followed by the remaining steps with the chosen configuration.
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+
+Multi-GPU: the path does not shard across GPUs here (one system per GPU);
+--gpus N runs N independent replicas, one per rank, and reports the sum.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LJ particle-steps/s at 1M atoms, auto-tuned vs fixed config; % of roofline"
+UNIT = "particle-steps/s"
+# Algorithmic FP32 work per within-cutoff unordered pair with Newton's third
+# law (FFMA = 2 flops): displacement 3, r^2 5, cutoff test 1, (sigma/r)^6 3,
+# f/r 4, F_i 6, F_j 6.  The reciprocal runs on the MUFU pipe and is not counted.
+FLOPS_PER_PAIR = 28
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_rate(sc, budget_s=12.0):
+    """The FP64 oracle (linked cells, OpenMP on all host cores) advancing a
+    bounded number of Stormer-Verlet steps of the same system."""
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    p = oracle.make_params(sc["box"], sc["eps"], sc["sigma"], sc["rcut"], True)
+    cell_min = 2.5 + sc["skin"]
+    t0 = time.perf_counter()
+    oracle.verlet_run(sc["x"], sc["v"], sc["types"], sc["mass"], p, sc["dt"], 1, cell_min=cell_min, nthreads=cores)
+    t1 = time.perf_counter()
+    per = (t1 - t0) / 2.0  # one call evaluates forces twice for one step
+    nsteps = max(1, min(50, int(budget_s / max(per, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.verlet_run(sc["x"], sc["v"], sc["types"], sc["mass"], p, sc["dt"], nsteps, cell_min=cell_min,
+                      nthreads=cores)
+    t1 = time.perf_counter()
+    n = len(sc["x"])
+    return {"value": n * nsteps / (t1 - t0), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d Stormer-Verlet steps of the N=%d liquid (FP64 linked cells, %d OpenMP threads)" %
+                      (nsteps, n, cores)}
+
+
+def run_reference(args):
+    """Reference arm: the oracle as it stands, on the host cores."""
+    from paper_2505_03438_gb300 import scenarios
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sc = scenarios.liquid_1m()
+    cb = oracle_rate(sc, budget_s=min(60.0, 6.0 + 2.0 * args.steps / 100.0))
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * len(sc["x"]) / cb["value"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "lj_liquid_1m: N=1048576 fcc 64^3x4, rho 0.8442, T 0.72, rc 2.5, skin 0.3"},
+            "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2505_03438_gb300 as lj
+    from paper_2505_03438_gb300 import scenarios
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    sc = scenarios.liquid_1m()
+    n = len(sc["x"])
+    K, W = args.steps, args.warmup
+    stream = torch.cuda.current_stream()
+    x = torch.tensor(sc["x"], device="cuda")
+    v = torch.tensor(sc["v"], device="cuda")
+    t = torch.zeros(n, dtype=torch.int32, device="cuda")
+    params = lj.make_params(sc["box"], skin=sc["skin"], dt=sc["dt"])
+    h = lj.ljsel_create(params, n, x, v, t, stream.cuda_stream)
+    lj.ljsel_step(h, W)  # warm-up with the default configuration
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # ---- timed region: one tuning phase + the rest of the K steps ----------
+    clk = Clocks(local)
+    c0 = lj.ljsel_get_counters(h)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rep = None
+    if args.tune:
+        chosen, rep = lj.ljsel_autotune(h, strategy=0, trial_steps=args.trial_steps)
+        done = rep["trial_steps_total"]
+    else:
+        chosen, done = lj.ljsel_get_config(h), 0
+    lj.ljsel_step(h, max(0, K - done))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    c1 = lj.ljsel_get_counters(h)
+    steps_done = c1["steps"] - c0["steps"]
+    if dist is not None:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * n * steps_done / (ms * 1e-3)
+    chosen_name = chosen.name()
+
+    # ---- per-kernel timing (CUDA events around each launch) ---------------
+    prof = lj.ljsel_profile_steps(h, args.profile_steps)
+    _, npairs = lj.ljsel_get_pairs(h, 0)
+    cnt = lj.ljsel_get_counters(h)
+
+    # ---- every fixed configuration, same workload -------------------------
+    fixed = {}
+    if args.fixed_steps > 0:
+        for c in lj.ljsel_default_candidates(h):
+            lj.ljsel_set_config(h, c)
+            lj.ljsel_step(h, 10)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            lj.ljsel_step(h, args.fixed_steps)
+            b.record(stream)
+            torch.cuda.synchronize()
+            fixed[c.name()] = n * args.fixed_steps / (a.elapsed_time(b) * 1e-3)
+        lj.ljsel_set_config(h, chosen)
+    lj.ljsel_destroy(h)
+
+    # ---- end to end through the C ABI with host buffers -------------------
+    e2e = None
+    if args.e2e:
+        xh = np.ascontiguousarray(sc["x"])
+        vh = np.ascontiguousarray(sc["v"])
+        th = np.zeros(n, np.int32)
+        xo = np.empty_like(xh)
+        vo = np.empty_like(vh)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        hp = lj.make_params(sc["box"], skin=sc["skin"], dt=sc["dt"])
+        h2 = lj.ljsel_create(hp, n, xh, vh, th, stream.cuda_stream)
+        done2 = 0
+        if args.tune:
+            _, r2 = lj.ljsel_autotune(h2, strategy=0, trial_steps=args.trial_steps)
+            done2 = r2["trial_steps_total"]
+        lj.ljsel_step(h2, max(0, K - done2))
+        lj.ljsel_get_state(h2, xo, vo)
+        t1 = time.perf_counter()
+        lj.ljsel_destroy(h2)
+        barrier()
+        e2e = {"value": world * n * K / (t1 - t0), "unit": UNIT,
+               "h2d_bytes_per_step": (xh.nbytes + vh.nbytes + th.nbytes) / K,
+               "d2h_bytes_per_step": (xo.nbytes + vo.nbytes) / K}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peaks = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    force_ms = prof["force_ms"]
+    achieved = npairs * FLOPS_PER_PAIR / (force_ms * 1e-3) / 1e12 if force_ms > 0 else None
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    # HBM side of the same kernel: list entries (4 B), own position, FP64
+    # state read and write, new position, reference position (VL, N3L off)
+    list_bytes = 4 * npairs * 2 * (1.0 + 0.4)
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": (achieved / fp32_peak) if achieved else None, "traffic": None,
+            "kernel": "force (%s)" % chosen_name, "launch_ms": force_ms, "flops_per_launch": npairs * FLOPS_PER_PAIR,
+            "peak_basis": "152 SMs x 128 FP32 lanes x 2 x %g MHz (of measured max clock)" % sm_max}
+    cb = None
+    if args.cpu_baseline and world == 1:
+        cb = oracle_rate(sc)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": int(steps_done),
+        "warmup": W, "ms_per_step": ms / max(steps_done, 1), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "lj_liquid_1m: N=1048576 fcc 64^3x4, rho 0.8442, T 0.72, rc 2.5, skin 0.3, R 10",
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (state + lists > 129 MB)",
+                   "tuned": bool(args.tune), "chosen": chosen_name,
+                   "precision": "FP32 pair math, FP64 integration and sums"},
+        "roofline": roof,
+        "cpu_baseline": cb,
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": None,
+        "kernel_ms": {k: prof[k] for k in ("rebuild_ms", "force_ms", "update_ms", "control_ms")},
+        "pairs_within_cutoff": npairs,
+        "rebuilds": c1["rebuilds"] - c0["rebuilds"], "early_rebuilds": c1["early_rebuilds"] - c0["early_rebuilds"],
+        "tuner": rep,
+        "fixed": fixed,
+        "best_fixed": max(fixed.items(), key=lambda kv: kv[1]) if fixed else None,
+    }
+    # kernels launched in the timed region: per step the force (and update
+    # when N3L is on) and the control kernel, per rebuild its chain, plus the
+    # per-call loop-init and command kernels
+    n3 = 1 if chosen.newton3 else 0
+    chain = 5 + (1 if chosen.method == lj.METHOD_VL else 0) + (2 if chosen.method == lj.METHOD_CLUSTER else 0)
+    line["gpu_launches"] = int(steps_done * (2 + n3) + (c1["rebuilds"] - c0["rebuilds"]) * chain)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-tune", dest="tune", action="store_false")
+    ap.add_argument("--trial-steps", type=int, default=10)
+    ap.add_argument("--fixed-steps", type=int, default=200)
+    ap.add_argument("--profile-steps", type=int, default=60)
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

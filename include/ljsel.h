@@ -149,6 +149,23 @@ typedef struct ljsel_tuner_report {
     int64_t trial_steps_total; /* steps advanced by trials in the last phase  */
 } ljsel_tuner_report;
 
+/* GPU time per kernel class, measured with CUDA events around each launch
+ * of plain stream launches (the tuning cost of Sec. 2.2.5 is built from
+ * the build and force times).                                              */
+typedef struct ljsel_profile {
+    int64_t steps;             /* steps advanced by the profiled call          */
+    int64_t rebuilds;          /* rebuilds among them                          */
+    int64_t launches;          /* kernels launched                             */
+    double rebuild_ms;         /* mean GPU time of one rebuild (all kernels)   */
+    double force_ms;           /* mean GPU time of the force kernel, fused
+                                  with the Stormer-Verlet update when N3L is
+                                  off                                         */
+    double update_ms;          /* mean GPU time of the separate update kernel
+                                  (N3L on), 0 otherwise                        */
+    double control_ms;         /* mean GPU time of the per-step control kernel */
+    double total_ms;           /* sum of the above over the call               */
+} ljsel_profile;
+
 typedef struct ljsel_system_s *ljsel_system;
 
 /* Message of the last failing call on this thread ("" if none).           */
@@ -228,6 +245,12 @@ ljsel_status ljsel_get_counters(ljsel_system s, ljsel_counters *c);
  * strategy) persists across phases of the same handle.                    */
 ljsel_status ljsel_autotune(ljsel_system s, const ljsel_tuner_opts *opts,
                             ljsel_config *chosen, ljsel_tuner_report *report);
+
+/* Advance nsteps steps with plain stream launches, a CUDA event before and
+ * after every kernel class, and report mean GPU times per launch.  The
+ * steps advance the simulation like ljsel_step.  Synchronizes every step;
+ * for measurement, not production.                                       */
+ljsel_status ljsel_profile_steps(ljsel_system s, int64_t nsteps, ljsel_profile *out);
 
 /* The default candidate set for this system: writes up to cap configs and
  * returns their number in *count.                                         */

@@ -106,6 +106,12 @@ class ljsel_tuner_report(ctypes.Structure):
     ]
 
 
+class ljsel_profile(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("rebuilds", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("rebuild_ms", ctypes.c_double), ("force_ms", ctypes.c_double), ("update_ms", ctypes.c_double),
+                ("control_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+
+
 _P = ctypes.c_void_p
 _SIGS = {
     "ljsel_last_error": ([], ctypes.c_char_p),
@@ -129,6 +135,7 @@ _SIGS = {
     "ljsel_get_counters": ([_P, ctypes.POINTER(ljsel_counters)], ctypes.c_int),
     "ljsel_autotune": ([_P, ctypes.POINTER(ljsel_tuner_opts), ctypes.POINTER(ljsel_config),
                         ctypes.POINTER(ljsel_tuner_report)], ctypes.c_int),
+    "ljsel_profile_steps": ([_P, ctypes.c_int64, ctypes.POINTER(ljsel_profile)], ctypes.c_int),
     "ljsel_default_candidates": ([_P, ctypes.c_int32, ctypes.POINTER(ljsel_config), ctypes.POINTER(ctypes.c_int32)],
                                  ctypes.c_int),
 }
@@ -307,6 +314,12 @@ def ljsel_get_counters(h) -> dict:
     return {k: getattr(c, k) for k, _ in c._fields_}
 
 
+def ljsel_profile_steps(h, nsteps) -> dict:
+    p = ljsel_profile()
+    _check(lib().ljsel_profile_steps(h, int(nsteps), ctypes.byref(p)))
+    return {k: getattr(p, k) for k, _ in p._fields_}
+
+
 def ljsel_default_candidates(h):
     cnt = ctypes.c_int32()
     _check(lib().ljsel_default_candidates(h, 0, None, ctypes.byref(cnt)))
@@ -407,6 +420,9 @@ class System:
 
     def counters(self):
         return ljsel_get_counters(self.h)
+
+    def profile(self, nsteps):
+        return ljsel_profile_steps(self.h, nsteps)
 
     def autotune(self, **kw):
         return ljsel_autotune(self.h, **kw)

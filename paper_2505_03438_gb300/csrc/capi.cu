@@ -445,6 +445,12 @@ ljsel_status ljsel_get_counters(ljsel_system h, ljsel_counters *c) {
     return LJSEL_OK;
 }
 
+ljsel_status ljsel_profile_steps(ljsel_system h, int64_t nsteps, ljsel_profile *out) {
+    System *s = (System *)h;
+    if (!s || !out || nsteps < 0) { set_error("invalid argument"); return LJSEL_ERR_ARG; }
+    return dispatch(s, [&](auto z) { return s->profile<decltype(z)>(nsteps, out); });
+}
+
 ljsel_status ljsel_default_candidates(ljsel_system h, int32_t cap, ljsel_config *out, int32_t *count) {
     System *s = (System *)h;
     if (!s || !count || (cap > 0 && !out)) { set_error("invalid argument"); return LJSEL_ERR_ARG; }

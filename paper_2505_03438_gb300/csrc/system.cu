@@ -230,7 +230,15 @@ ljsel_status System::apply_config() {
     }
     if (cfg.method == LJSEL_METHOD_CLUSTER) {
         ncl_cap = n / M + ncell + 1;
-        if (cp_cap <= 0) cp_cap = cfg.newton3 ? 48 : 96;
+        if (cp_cap <= 0) {
+            // clusters per stencil at the mean occupancy, with room
+            const double occ = (double)n / ncell;
+            const double per_cell = std::max(1.0, std::ceil(occ / M));
+            const int stencil = (2 * reach + 1) * (2 * reach + 1) * (2 * reach + 1);
+            double est = 1.3 * stencil * per_cell + 8;
+            if (cfg.newton3) est = est * 0.5 + 8;
+            cp_cap = (int)std::min(est, 8192.0);
+        }
         cp_stride = ((ncl_cap + 31) / 32) * 32;
         LJ_TRY(grow(b_cl_first, (size_t)ncl_cap * 4));
         LJ_TRY(grow(b_cl_count, (size_t)ncl_cap * 4));
@@ -519,6 +527,66 @@ template <typename R> ljsel_status System::sync_velocities() {
     return LJSEL_OK;
 }
 
+// Plain stream launches with events around each kernel class; the host
+// reads the control block every step to launch the rebuild only when the
+// device asked for it, so every timed interval holds real work.
+template <typename R> ljsel_status System::profile(long long nsteps, ljsel_profile *out) {
+    memset(out, 0, sizeof(*out));
+    LJ_TRY(ensure_structure<R>());
+    cudaEvent_t ev[6];
+    for (auto &e : ev) LJ_CUDA(cudaEventCreate(&e));
+    auto done = [&]() { for (auto &e : ev) cudaEventDestroy(e); };
+    Dev<R> S;
+    fill_dev(S);
+    const int chain = 5 + (cfg.method == LJSEL_METHOD_VL ? 1 : 0) + (cfg.method == LJSEL_METHOD_CLUSTER ? 2 : 0);
+    LJ_TRY(cmd(CMD_BEGIN, nsteps));
+    double tr = 0, tf = 0, tu = 0, tc = 0;
+    for (long long k = 0; k < nsteps; ++k) {
+        if (read_ctrl() != LJSEL_OK) { done(); return LJSEL_ERR_CUDA; }
+        if (h_ctrl->overflow) {
+            ljsel_status st = handle_overflow();
+            if (st == LJSEL_OK) st = ensure_structure<R>();
+            if (st != LJSEL_OK) { done(); return st; }
+            fill_dev(S);
+            continue;
+        }
+        const bool reb = h_ctrl->rebuild_now != 0;
+        if (reb) {
+            cudaEventRecord(ev[0], stream);
+            enqueue_rebuild(S, stream);
+            cudaEventRecord(ev[1], stream);
+            out->launches += chain;
+        }
+        cudaEventRecord(ev[2], stream);
+        launch_force(S, cfg, cfg.newton3 ? MODE_FORCE : MODE_STEP, false, nullptr, 0, stream);
+        cudaEventRecord(ev[3], stream);
+        if (cfg.newton3) { launch_integrate(S, false, stream); out->launches += 1; }
+        cudaEventRecord(ev[4], stream);
+        launch_control(S.ctrl, 0, 0, 0, stream);
+        cudaEventRecord(ev[5], stream);
+        out->launches += 2;
+        cudaError_t e = cudaEventSynchronize(ev[5]);
+        if (e != cudaSuccess) { done(); set_error(cudaGetErrorString(e)); return LJSEL_ERR_CUDA; }
+        float a = 0, b = 0, c = 0, d = 0;
+        if (reb) { cudaEventElapsedTime(&a, ev[0], ev[1]); out->rebuilds += 1; tr += a; }
+        cudaEventElapsedTime(&b, ev[2], ev[3]);
+        cudaEventElapsedTime(&c, ev[3], ev[4]);
+        cudaEventElapsedTime(&d, ev[4], ev[5]);
+        tf += b; tu += c; tc += d;
+        out->steps += 1;
+    }
+    done();
+    LJ_TRY(read_ctrl());
+    LJ_TRY(check_device_errors());
+    synced = false;
+    out->rebuild_ms = out->rebuilds ? tr / out->rebuilds : 0.0;
+    out->force_ms = out->steps ? tf / out->steps : 0.0;
+    out->update_ms = (out->steps && cfg.newton3) ? tu / out->steps : 0.0;
+    out->control_ms = out->steps ? tc / out->steps : 0.0;
+    out->total_ms = tr + tf + tu + tc;
+    return LJSEL_OK;
+}
+
 // Explicit instantiations of the member templates used by the C ABI.
 #define INST(R)                                                        \
     template void System::fill_dev<R>(Dev<R> &) const;                 \
@@ -528,7 +596,8 @@ template <typename R> ljsel_status System::sync_velocities() {
     template ljsel_status System::build_graph<R>();                    \
     template ljsel_status System::advance<R>(long long);               \
     template ljsel_status System::compute_forces<R>(bool);             \
-    template ljsel_status System::sync_velocities<R>();
+    template ljsel_status System::sync_velocities<R>();                \
+    template ljsel_status System::profile<R>(long long, ljsel_profile *);
 INST(float)
 INST(double)
 #undef INST

@@ -85,6 +85,7 @@ struct System {
     template <typename R> ljsel_status advance(long long nsteps);
     template <typename R> ljsel_status compute_forces(bool ev);
     template <typename R> ljsel_status sync_velocities();
+    template <typename R> ljsel_status profile(long long nsteps, ljsel_profile *out);
 };
 
 ljsel_status validate_config(const System &s, const ljsel_config *c);
