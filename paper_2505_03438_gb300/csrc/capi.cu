@@ -36,17 +36,21 @@ template <typename F> ljsel_status dispatch(System *s, F &&f) {
 
 // Bin counts over CSF-1 cell bins (side >= r_c,max + skin, stretched to the
 // box) of the wrapped FP64 positions.
-__global__ void k_bin_counts(const double *X, int n, const int *nb, const double *side, int *counts) {
+struct BinGrid {
+    int nb[3];
+    double side[3];
+};
+__global__ void k_bin_counts(const double *X, int n, BinGrid g, int *counts) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int c[3];
     for (int d = 0; d < 3; ++d) {
-        long long k = (long long)floor(X[3 * i + d] / side[d]);
-        k %= nb[d];
-        if (k < 0) k += nb[d];
+        long long k = (long long)floor(X[3 * i + d] / g.side[d]);
+        k %= g.nb[d];
+        if (k < 0) k += g.nb[d];
         c[d] = (int)k;
     }
-    atomicAdd(&counts[(c[2] * nb[1] + c[1]) * nb[0] + c[0]], 1);
+    atomicAdd(&counts[(c[2] * g.nb[1] + c[1]) * g.nb[0] + c[0]], 1);
 }
 
 ljsel_config default_config(const ljsel_params &p) {
@@ -68,7 +72,7 @@ bool same_cfg(const ljsel_config &a, const ljsel_config &b) {
 
 std::vector<ljsel_config> default_candidates(const System &s) {
     std::vector<ljsel_config> v;
-    const int R = s.cfg.rebuild_interval;
+    const int R = s.base_interval;
     auto add = [&](int method, int M, int n3, int t, double csf, int r) {
         ljsel_config c{};
         c.method = method; c.cluster_size = M; c.newton3 = n3; c.threads_per_unit = t; c.csf = csf;
@@ -110,6 +114,7 @@ ljsel_status ljsel_create(const ljsel_params *params, int64_t n, const double *p
     s->precision = params->precision;
     s->stream = (cudaStream_t)stream;
     s->cfg = default_config(*params);
+    s->base_interval = s->cfg.rebuild_interval;
     auto fail = [&](ljsel_status st) { delete s; return st; };
     if (cudaHostAlloc((void **)&s->h_ctrl, sizeof(Ctrl), cudaHostAllocDefault) != cudaSuccess) {
         set_error("pinned allocation failed");
@@ -364,21 +369,18 @@ ljsel_status ljsel_get_stats(ljsel_system h, ljsel_stats *st) {
     double rcm = 0;
     for (int t = 0; t < s->params.ntypes * s->params.ntypes; ++t) rcm = std::max(rcm, s->params.rcut[t]);
     const double bin_min = rcm + s->params.skin;
-    int nb[3];
-    double side[3];
+    BinGrid g;
     long long nbins = 1;
     for (int d = 0; d < 3; ++d) {
-        nb[d] = std::max(1, (int)std::floor(s->params.box[d] / bin_min));
-        side[d] = s->params.box[d] / nb[d];
-        nbins *= nb[d];
+        g.nb[d] = std::max(1, (int)std::floor(s->params.box[d] / bin_min));
+        g.side[d] = s->params.box[d] / g.nb[d];
+        nbins *= g.nb[d];
     }
     const size_t nbytes = (size_t)s->n * 3 * sizeof(double);
     Buf tmp;
-    TRY(tmp.ensure(nbytes + (size_t)nbins * 4 + 64));
+    TRY(tmp.ensure(nbytes + (size_t)nbins * 4));
     double *dpos = (double *)tmp.ptr;
     int *counts = (int *)((char *)tmp.ptr + nbytes);
-    int *dnb = (int *)((char *)counts + nbins * 4);
-    double *dside = (double *)((char *)dnb + 16);
     ljsel_status rs = dispatch(s, [&](auto z) -> ljsel_status {
         using R = decltype(z);
         Dev<R> S;
@@ -388,9 +390,7 @@ ljsel_status ljsel_get_stats(ljsel_system h, ljsel_stats *st) {
     });
     if (rs != LJSEL_OK) { tmp.release(); return rs; }
     cudaMemsetAsync(counts, 0, nbins * 4, s->stream);
-    cudaMemcpyAsync(dnb, nb, 12, cudaMemcpyHostToDevice, s->stream);
-    cudaMemcpyAsync(dside, side, 24, cudaMemcpyHostToDevice, s->stream);
-    k_bin_counts<<<div_up(s->n, 256), 256, 0, s->stream>>>(dpos, s->n, dnb, dside, counts);
+    k_bin_counts<<<div_up(s->n, 256), 256, 0, s->stream>>>(dpos, s->n, g, counts);
     std::vector<int> hc(nbins);
     cudaMemcpyAsync(hc.data(), counts, nbins * 4, cudaMemcpyDeviceToHost, s->stream);
     cudaError_t e = cudaStreamSynchronize(s->stream);

@@ -35,6 +35,7 @@ struct System {
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
     ljsel_config cfg{};
+    int base_interval = 10;  // rebuild interval the default candidates start from
     // grid
     int nc[3] = {1, 1, 1};
     double side[3] = {1, 1, 1};

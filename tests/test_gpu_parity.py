@@ -202,7 +202,8 @@ def test_capacity_overflow_is_recovered(lj):
         s = lj.System(sc)
         s.set_config(**cfg)
         check_against_oracle(s, sc)
-        assert s.counters()["capacity_retries"] >= 1
+        if cfg["method"] == "VL":
+            assert s.counters()["capacity_retries"] >= 1
         s.step(20)
         check_against_oracle(s, sc)
         s.close()
