@@ -256,6 +256,34 @@ ljsel_status ljsel_profile_steps(ljsel_system s, int64_t nsteps, ljsel_profile *
  * returns their number in *count.                                         */
 ljsel_status ljsel_default_candidates(ljsel_system s, int32_t cap, ljsel_config *out, int32_t *count);
 
+/* Allocation-free force evaluation.  The paper has no counterpart: this is
+ * a service for callers that cannot allocate device memory -- code running
+ * while a stream is captured into a CUDA graph, code inside a framework
+ * whose allocator owns all device memory, or latency-critical loops that
+ * must not enter the allocator.  It bins the particles into linked cells of
+ * side >= max r_cut (no skin) and evaluates the library's FP32 LJ pair
+ * arithmetic with the exact cutoff decision, using only a fixed 5.8 MB
+ * static device array inside the library (held by every GPU that loads the
+ * library until the process exits) and the caller's buffers.
+ *   params: as for ljsel_create; precision must be 0.
+ *   n: 1 .. 131072 particles; larger n, or a box needing more than 131072
+ *      cells, returns LJSEL_ERR_CAPACITY.
+ *   pos: device, n x 3 doubles (wrapped into the box on the fly);
+ *   types: device, n int32 in [0, ntypes) (NULL: all 0);
+ *   forces: device, n x 3 doubles, written in input order;
+ *   energy, virial: host doubles or NULL; when either is given the call
+ *      synchronizes the stream.
+ *   stream: cudaStream_t or NULL.
+ * The first call on a device resolves the address of the static array (with
+ * that device current); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents (each
+ * call clears what must start at zero); calls whose GPU work overlaps (on
+ * different streams or from different threads) race on it, so serialize
+ * them.  Calls no cudaMalloc, cudaFree or other allocating routine.        */
+ljsel_status ljsel_compute_forces_noalloc(const ljsel_params *params, int64_t n, const double *pos,
+                                          const int32_t *types, double *forces, double *energy, double *virial,
+                                          void *stream);
+
 #ifdef __cplusplus
 }
 #endif

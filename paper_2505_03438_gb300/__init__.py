@@ -135,6 +135,9 @@ _SIGS = {
     "ljsel_get_counters": ([_P, ctypes.POINTER(ljsel_counters)], ctypes.c_int),
     "ljsel_autotune": ([_P, ctypes.POINTER(ljsel_tuner_opts), ctypes.POINTER(ljsel_config),
                         ctypes.POINTER(ljsel_tuner_report)], ctypes.c_int),
+    "ljsel_compute_forces_noalloc": ([ctypes.POINTER(ljsel_params), ctypes.c_int64, _P, _P, _P,
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _P],
+                                     ctypes.c_int),
     "ljsel_profile_steps": ([_P, ctypes.c_int64, ctypes.POINTER(ljsel_profile)], ctypes.c_int),
     "ljsel_default_candidates": ([_P, ctypes.c_int32, ctypes.POINTER(ljsel_config), ctypes.POINTER(ctypes.c_int32)],
                                  ctypes.c_int),
@@ -318,6 +321,20 @@ def ljsel_profile_steps(h, nsteps) -> dict:
     p = ljsel_profile()
     _check(lib().ljsel_profile_steps(h, int(nsteps), ctypes.byref(p)))
     return {k: getattr(p, k) for k, _ in p._fields_}
+
+
+def ljsel_compute_forces_noalloc(params: ljsel_params, n, pos, forces, types=None, stream=None):
+    """Allocation-free force evaluation (device pos/types/forces); returns (energy, virial)."""
+    pp, d1 = _ptr(pos)
+    fp, d2 = _ptr(forces)
+    tp, d3 = _ptr(types)
+    if not (d1 and d2 and (types is None or d3)):
+        raise ValueError("pos, forces and types must be device tensors")
+    e = ctypes.c_double()
+    w = ctypes.c_double()
+    _check(lib().ljsel_compute_forces_noalloc(ctypes.byref(params), int(n), pp, tp, fp, ctypes.byref(e),
+                                              ctypes.byref(w), stream))
+    return e.value, w.value
 
 
 def ljsel_default_candidates(h):
