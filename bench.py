@@ -160,7 +160,10 @@ def run_ours(args):
     t = torch.zeros(n, dtype=torch.int32, device="cuda")
     params = lj.make_params(sc["box"], skin=sc["skin"], dt=sc["dt"])
     h = lj.ljsel_create(params, n, x, v, t, stream.cuda_stream)
-    lj.ljsel_step(h, W)  # warm-up with the default configuration
+    if args.method:
+        lj.ljsel_set_config(h, lj.make_config(args.method, cluster_size=args.cluster, newton3=args.newton3,
+                                              threads_per_unit=args.tpu, rebuild_interval=sc["rebuild"]))
+    lj.ljsel_step(h, W)  # warm-up
     torch.cuda.synchronize()
 
     def barrier():
@@ -290,7 +293,7 @@ def run_ours(args):
     # when N3L is on) and the control kernel, per rebuild its chain, plus the
     # per-call loop-init and command kernels
     n3 = 1 if chosen.newton3 else 0
-    chain = 5 + (1 if chosen.method == lj.METHOD_VL else 0) + (2 if chosen.method == lj.METHOD_CLUSTER else 0)
+    chain = 5 + {lj.METHOD_VL: 1, lj.METHOD_CLUSTER: 2, lj.METHOD_VLW: 2}.get(chosen.method, 0)
     line["gpu_launches"] = int(steps_done * (2 + n3) + (c1["rebuilds"] - c0["rebuilds"]) * chain)
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -304,6 +307,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-tune", dest="tune", action="store_false")
+    ap.add_argument("--method", default=None, help="with --no-tune: run this fixed method (LC, VL, VLW, CL)")
+    ap.add_argument("--newton3", action="store_true")
+    ap.add_argument("--tpu", type=int, default=1)
+    ap.add_argument("--cluster", type=int, default=8)
     ap.add_argument("--trial-steps", type=int, default=10)
     ap.add_argument("--fixed-steps", type=int, default=200)
     ap.add_argument("--profile-steps", type=int, default=60)

@@ -57,9 +57,14 @@ typedef enum ljsel_method {
                                   particles of the cells within reach (no list)  */
     LJSEL_METHOD_VL = 1,       /* Verlet lists: per-particle lists of neighbours
                                   within r_c + skin, rebuilt every R steps        */
-    LJSEL_METHOD_CLUSTER = 2   /* cluster-pair Verlet lists: groups of M spatially
+    LJSEL_METHOD_CLUSTER = 2,  /* cluster-pair Verlet lists: groups of M spatially
                                   sorted particles, lists of j-clusters per
                                   i-cluster (M = 4, 8 or 32)                      */
+    LJSEL_METHOD_VLW = 3       /* Verlet lists over shared-memory windows: cells are
+                                  cut into strips of <= 128 particles, each CTA
+                                  stages its strip's neighbourhood (<= 2047
+                                  particles) on chip and list entries are 16-bit
+                                  window slots (CSF 1, one thread per particle)   */
 } ljsel_method;
 
 /* System parameters.  eps/sigma/rcut are ntypes x ntypes row-major and must

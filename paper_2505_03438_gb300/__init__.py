@@ -21,8 +21,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libljsel.so")
 MAX_TYPES = 4
 
-METHOD_LC, METHOD_VL, METHOD_CLUSTER = 0, 1, 2
-METHOD_NAMES = {METHOD_LC: "LC", METHOD_VL: "VL", METHOD_CLUSTER: "CL"}
+METHOD_LC, METHOD_VL, METHOD_CLUSTER, METHOD_VLW = 0, 1, 2, 3
+METHOD_NAMES = {METHOD_LC: "LC", METHOD_VL: "VL", METHOD_CLUSTER: "CL", METHOD_VLW: "VLW"}
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_CAPACITY", 5: "ERR_BOX",
           6: "ERR_NONFINITE", 7: "ERR_TIMEOUT", 8: "ERR_STATE", 9: "ERR_UNSUPPORTED"}
@@ -211,7 +211,8 @@ def make_params(box, eps=1.0, sigma=1.0, rcut=2.5, mass=1.0, skin=0.3, dt=0.005,
 
 def make_config(method="VL", cluster_size=1, newton3=False, threads_per_unit=1, rebuild_interval=10, csf=1.0):
     c = ljsel_config()
-    c.method = {"LC": METHOD_LC, "VL": METHOD_VL, "CL": METHOD_CLUSTER, "CLUSTER": METHOD_CLUSTER}.get(method, method)
+    c.method = {"LC": METHOD_LC, "VL": METHOD_VL, "CL": METHOD_CLUSTER, "CLUSTER": METHOD_CLUSTER,
+                "VLW": METHOD_VLW}.get(method, method)
     c.cluster_size = int(cluster_size)
     c.newton3 = 1 if newton3 else 0
     c.threads_per_unit = int(threads_per_unit)

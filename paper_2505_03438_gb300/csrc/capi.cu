@@ -85,6 +85,8 @@ std::vector<ljsel_config> default_candidates(const System &s) {
     for (int t : {1, 4}) add(LJSEL_METHOD_VL, 1, 1, t, 1.0, R);
     add(LJSEL_METHOD_VL, 1, 0, 1, 1.0, 2 * R);
     add(LJSEL_METHOD_VL, 1, 0, 2, 1.0, 2 * R);
+    for (int n3 = 0; n3 <= 1; ++n3) add(LJSEL_METHOD_VLW, 1, n3, 1, 1.0, R);
+    add(LJSEL_METHOD_VLW, 1, 0, 1, 1.0, 2 * R);
     for (int M : {4, 8, 32}) {
         for (int t = M; t <= 32; t *= 2) add(LJSEL_METHOD_CLUSTER, M, 0, t, 1.0, R);
         add(LJSEL_METHOD_CLUSTER, M, 1, M, 1.0, R);
@@ -432,8 +434,8 @@ ljsel_status ljsel_get_counters(ljsel_system h, ljsel_counters *c) {
     c->early_rebuilds = s->h_ctrl->early_rebuilds;
     c->ncells = s->ncell;
     c->capacity_retries = s->capacity_retries;
-    if (s->cfg.method == LJSEL_METHOD_VL) {
-        c->list_capacity = (int64_t)s->nl_cap * s->n;
+    if (s->cfg.method == LJSEL_METHOD_VL || s->cfg.method == LJSEL_METHOD_VLW) {
+        c->list_capacity = (int64_t)s->nl_cap * s->n;  // row-major, nl_cap per particle
         c->list_entries = s->h_ctrl->need_cap;  // longest row of the last build
     } else if (s->cfg.method == LJSEL_METHOD_CLUSTER) {
         int ncl = 0;

@@ -16,8 +16,6 @@ namespace {
 
 constexpr int FORCE_THREADS = 128;
 
-__device__ __forceinline__ int floor_div(int a, int b) { int q = a / b; return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q; }
-
 // Shared-memory copy of the per-type-pair table for multi-type systems.
 template <typename R> struct STab {
     R sig2[MAXT2], e24[MAXT2], e48[MAXT2], e4[MAXT2], ushift[MAXT2], lo[MAXT2], hi[MAXT2];
@@ -153,12 +151,37 @@ __device__ __forceinline__ void export_pair(const Dev<R> &S, int sp, int i, int 
 }
 
 // ---------------------------------------------------------------------------
-// Verlet lists.  Thread group of `tpp` lanes per particle i (sorted index);
-// lane `sub` takes list entries sub, sub + tpp, ...; the group sums F_i by
-// shuffles.  N3L off: full lists, F_j untouched.  N3L on: half lists, -F_ij
-// added to F_j with a vector atomic.
+// Verlet lists.  Thread group of `tpp` lanes per particle i (sorted index).
+// The front of the row (entries without an image, padded with the sentinel)
+// is read in 16-byte chunks sub, sub + tpp, ...; the next chunk is loaded
+// before the current chunk's four positions are gathered.  The few entries
+// with a periodic image, at the back of the row, take the exact image
+// arithmetic.  The group sums F_i by shuffles.  Thread 0 of each block first
+// asks the L2 to prefetch the block's contiguous list rows and state with
+// one bulk-prefetch instruction each.  N3L off: full lists, F_j untouched.
+// N3L on: half lists, -F_ij added to F_j with a vector atomic.
+__device__ __forceinline__ void l2_prefetch(const void *p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 template <typename R, bool N3L, int MODE, bool EV, bool MT>
-__global__ void __launch_bounds__(FORCE_THREADS) k_vl(Dev<R> S, int tpp, int2 *pairs, long long cap) {
+__device__ __forceinline__ void vl_pair(const Dev<R> &S, const STab<R> &T, const V4<R> &pi, int ti, int i, int sp,
+                                        int j, int sx, int sy, int sz, R dx, R dy, R dz, const V4<R> &pj, Acc<R> &a,
+                                        int2 *pairs, long long cap) {
+    const R r2 = r2_of(dx, dy, dz);
+    const int tp = MT ? ti * S.tab.ntypes + type_of(pj) : 0;
+    bool in;
+    const R fr = pair_term<R, MT, EV>(S, T, tp, r2, pi, pj, sx, sy, sz, a, in);
+    if (MODE == MODE_PAIRS) {
+        if (in && (N3L || S.id[sp][i] < S.id[sp][j])) export_pair(S, sp, i, j, pairs, cap);
+        return;
+    }
+    a.fx += fr * dx; a.fy += fr * dy; a.fz += fr * dz;
+    if (N3L && in) add_force(S.force, j, -fr * dx, -fr * dy, -fr * dz);
+}
+
+template <typename R, bool N3L, int MODE, bool EV, bool MT>
+__global__ void __launch_bounds__(FORCE_THREADS, 8) k_vl(Dev<R> S, int tpp, int2 *pairs, long long cap) {
     Ctrl *C = S.ctrl;
     if (C->overflow) return;
     __shared__ STab<R> T;
@@ -168,38 +191,56 @@ __global__ void __launch_bounds__(FORCE_THREADS) k_vl(Dev<R> S, int tpp, int2 *p
     const bool valid = i < S.n;
     const int pp = C->pos_par, sp = C->state_par;
     const V4<R> *P = S.pos[pp];
-    V4<R> pi;
-    int cnt = 0, ti = 0;
-    if (valid) { pi = ldpos(P, i); cnt = S.nl_count[i]; ti = type_of(pi); }
-    Acc<R> a;
-    for (int k = sub; k < cnt; k += tpp) {
-        const uint32_t e = S.nl[(size_t)k * S.nl_stride + i];
-        const int j = (int)(e & JMASK);
-        const uint32_t code = e >> JBITS;
-        const V4<R> pj = ldpos(P, j);
-        int sx = 0, sy = 0, sz = 0;
-        R dx, dy, dz;
-        if (code == 0) {
-            dx = pi.x - pj.x; dy = pi.y - pj.y; dz = pi.z - pj.z;
-        } else {
-            decode_image(code, sx, sy, sz);
-            dx = image_dx(pi.x, pj.x, sx, S.box[0], S.box_lo[0]);
-            dy = image_dx(pi.y, pj.y, sy, S.box[1], S.box_lo[1]);
-            dz = image_dx(pi.z, pj.z, sz, S.box[2], S.box_lo[2]);
-        }
-        const R r2 = r2_of(dx, dy, dz);
-        const int tp = MT ? ti * S.tab.ntypes + type_of(pj) : 0;
-        bool in;
-        const R fr = pair_term<R, MT, EV>(S, T, tp, r2, pi, pj, sx, sy, sz, a, in);
-        if (MODE == MODE_PAIRS) {
-            if (in) {
-                if (N3L) export_pair(S, sp, i, j, pairs, cap);
-                else if (S.id[sp][i] < S.id[sp][j]) export_pair(S, sp, i, j, pairs, cap);
+    if (threadIdx.x == 0) {
+        const int i0 = (blockIdx.x * blockDim.x) / tpp;
+        const int nrow = min(blockDim.x / tpp, S.n - i0);
+        if (nrow > 0) {
+            l2_prefetch(S.nl + (size_t)i0 * S.nl_cap, (unsigned)(nrow * S.nl_cap * 4));
+            // bulk prefetch wants 16-byte aligned start and size: a slice of
+            // doubles qualifies when its first index and its length are even
+            if (MODE == MODE_STEP && (nrow & 1) == 0) {
+                for (int d = 0; d < 3; ++d) {
+                    const size_t first = (size_t)d * S.n + i0;
+                    if ((first & 1) != 0) continue;
+                    l2_prefetch(S.x[sp] + first, (unsigned)(nrow * 8));
+                    l2_prefetch(S.v[sp] + first, (unsigned)(nrow * 8));
+                }
             }
-            continue;
         }
-        a.fx += fr * dx; a.fy += fr * dy; a.fz += fr * dz;
-        if (N3L && in) add_force(S.force, j, -fr * dx, -fr * dy, -fr * dz);
+    }
+    V4<R> pi = make_pos((R)0, (R)0, (R)0, 0);
+    int nq = 0, nb = 0, ti = 0;
+    const uint32_t *rowp = nullptr;
+    if (valid) {
+        pi = ldpos(P, i);
+        const int cnt = S.nl_count[i];
+        nq = ((cnt & 0xffff) + 3) >> 2;
+        nb = cnt >> 16;
+        ti = type_of(pi);
+        rowp = S.nl + (size_t)i * S.nl_cap;
+    }
+    const uint4 *row = reinterpret_cast<const uint4 *>(rowp);
+    Acc<R> a;
+    uint4 e = sub < nq ? __ldg(row + sub) : make_uint4(0, 0, 0, 0);
+    for (int q = sub; q < nq; q += tpp) {
+        const uint4 en = q + tpp < nq ? __ldg(row + q + tpp) : e;
+        const V4<R> p0 = ldpos(P, (int)e.x), p1 = ldpos(P, (int)e.y), p2 = ldpos(P, (int)e.z), p3 = ldpos(P, (int)e.w);
+        vl_pair<R, N3L, MODE, EV, MT>(S, T, pi, ti, i, sp, (int)e.x, 0, 0, 0, pi.x - p0.x, pi.y - p0.y, pi.z - p0.z, p0, a, pairs, cap);
+        vl_pair<R, N3L, MODE, EV, MT>(S, T, pi, ti, i, sp, (int)e.y, 0, 0, 0, pi.x - p1.x, pi.y - p1.y, pi.z - p1.z, p1, a, pairs, cap);
+        vl_pair<R, N3L, MODE, EV, MT>(S, T, pi, ti, i, sp, (int)e.z, 0, 0, 0, pi.x - p2.x, pi.y - p2.y, pi.z - p2.z, p2, a, pairs, cap);
+        vl_pair<R, N3L, MODE, EV, MT>(S, T, pi, ti, i, sp, (int)e.w, 0, 0, 0, pi.x - p3.x, pi.y - p3.y, pi.z - p3.z, p3, a, pairs, cap);
+        e = en;
+    }
+    for (int k = sub; k < nb; k += tpp) {
+        const uint32_t ent = rowp[S.nl_cap - 1 - k];
+        const int j = (int)(ent & JMASK);
+        int sx, sy, sz;
+        decode_image(ent >> JBITS, sx, sy, sz);
+        const V4<R> pj = ldpos(P, j);
+        vl_pair<R, N3L, MODE, EV, MT>(S, T, pi, ti, i, sp, j, sx, sy, sz,
+                                      image_dx(pi.x, pj.x, sx, S.box[0], S.box_lo[0]),
+                                      image_dx(pi.y, pj.y, sy, S.box[1], S.box_lo[1]),
+                                      image_dx(pi.z, pj.z, sz, S.box[2], S.box_lo[2]), pj, a, pairs, cap);
     }
     if (MODE == MODE_PAIRS) return;
     for (int o = tpp >> 1; o > 0; o >>= 1) {
@@ -244,41 +285,43 @@ __global__ void __launch_bounds__(FORCE_THREADS) k_lc(Dev<R> S, int2 *pairs, lon
         const int cx = c % S.nc[0], cy = (c / S.nc[0]) % S.nc[1], cz = c / (S.nc[0] * S.nc[1]);
         const int rch = S.reach;
         for (int oz = -rch; oz <= rch; ++oz) {
-            int rz = cz + oz, sz = floor_div(rz, S.nc[2]);
-            if (sz < -1 || sz > 1) continue;
-            int wz = rz - sz * S.nc[2];
+            int wz, sz;
+            if (!wrap_cell(cz, oz, S.nc[2], wz, sz)) continue;
             for (int oy = -rch; oy <= rch; ++oy) {
-                int ry = cy + oy, sy = floor_div(ry, S.nc[1]);
-                if (sy < -1 || sy > 1) continue;
-                int wy = ry - sy * S.nc[1];
+                int wy, sy;
+                if (!wrap_cell(cy, oy, S.nc[1], wy, sy)) continue;
                 for (int ox = -rch; ox <= rch; ++ox) {
-                    int rx = cx + ox, sx = floor_div(rx, S.nc[0]);
-                    if (sx < -1 || sx > 1) continue;
-                    int wx = rx - sx * S.nc[0];
+                    int wx, sx;
+                    if (!wrap_cell(cx, ox, S.nc[0], wx, sx)) continue;
                     const int cc = (wz * S.nc[1] + wy) * S.nc[0] + wx;
                     const bool img = (sx | sy | sz) != 0;
                     const int jb = S.cell_start[cc], je = S.cell_start[cc + 1];
-                    for (int j = N3L ? max(jb, i + 1) : jb; j < je; ++j) {
-                        if (!N3L && j == i && !img) continue;
-                        const V4<R> pj = ldpos(P, j);
-                        R dx, dy, dz;
-                        if (!img) {
-                            dx = pi.x - pj.x; dy = pi.y - pj.y; dz = pi.z - pj.z;
-                        } else {
-                            dx = image_dx(pi.x, pj.x, sx, S.box[0], S.box_lo[0]);
-                            dy = image_dx(pi.y, pj.y, sy, S.box[1], S.box_lo[1]);
-                            dz = image_dx(pi.z, pj.z, sz, S.box[2], S.box_lo[2]);
-                        }
+                    // one pair; the exact image arithmetic only in image cells
+                    auto one = [&](int j, R dx, R dy, R dz, const V4<R> &pj) {
                         const R r2 = r2_of(dx, dy, dz);
                         const int tp = MT ? ti * S.tab.ntypes + type_of(pj) : 0;
                         bool in;
                         const R fr = pair_term<R, MT, EV>(S, T, tp, r2, pi, pj, sx, sy, sz, a, in);
                         if (MODE == MODE_PAIRS) {
                             if (in && (N3L || S.id[sp][i] < S.id[sp][j])) export_pair(S, sp, i, j, pairs, cap);
-                            continue;
+                            return;
                         }
                         a.fx += fr * dx; a.fy += fr * dy; a.fz += fr * dz;
                         if (N3L && in) add_force(S.force, j, -fr * dx, -fr * dy, -fr * dz);
+                    };
+                    if (!img) {
+                        for (int j = N3L ? max(jb, i + 1) : jb; j < je; ++j) {
+                            if (!N3L && j == i) continue;
+                            const V4<R> pj = ldpos(P, j);
+                            one(j, pi.x - pj.x, pi.y - pj.y, pi.z - pj.z, pj);
+                        }
+                    } else {
+                        for (int j = N3L ? max(jb, i + 1) : jb; j < je; ++j) {
+                            const V4<R> pj = ldpos(P, j);
+                            one(j, image_dx(pi.x, pj.x, sx, S.box[0], S.box_lo[0]),
+                                image_dx(pi.y, pj.y, sy, S.box[1], S.box_lo[1]),
+                                image_dx(pi.z, pj.z, sz, S.box[2], S.box_lo[2]), pj);
+                        }
                     }
                 }
             }
@@ -488,12 +531,14 @@ template <typename R> void launch_cp_force(const Dev<R> &S, const ljsel_config &
 template <> void launch_force<float>(const Dev<float> &S, const ljsel_config &cfg, int mode, bool ev, int2 *pairs,
                                      long long cap, cudaStream_t st) {
     if (cfg.method == LJSEL_METHOD_CLUSTER) { launch_cp_force<float>(S, cfg, mode, ev, pairs, cap, st); return; }
+    if (cfg.method == LJSEL_METHOD_VLW) { launch_vlw_force<float>(S, cfg, mode, ev, pairs, cap, st); return; }
     if (S.tab.ntypes > 1) force_dispatch<float, true>(S, cfg, mode, ev, pairs, cap, st);
     else force_dispatch<float, false>(S, cfg, mode, ev, pairs, cap, st);
 }
 template <> void launch_force<double>(const Dev<double> &S, const ljsel_config &cfg, int mode, bool ev, int2 *pairs,
                                       long long cap, cudaStream_t st) {
     if (cfg.method == LJSEL_METHOD_CLUSTER) { launch_cp_force<double>(S, cfg, mode, ev, pairs, cap, st); return; }
+    if (cfg.method == LJSEL_METHOD_VLW) { launch_vlw_force<double>(S, cfg, mode, ev, pairs, cap, st); return; }
     force_dispatch<double, true>(S, cfg, mode, ev, pairs, cap, st);
 }
 

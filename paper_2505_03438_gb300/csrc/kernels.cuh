@@ -16,6 +16,11 @@ template <typename R> void launch_vl_build(const Dev<R> &S, bool n3l, cudaStream
 template <typename R> void launch_cluster_form(const Dev<R> &S, cudaStream_t st);
 template <typename R> void launch_cp_build(const Dev<R> &S, bool n3l, cudaStream_t st);
 void launch_rebuild_finish(Ctrl *C, cudaStream_t st);
+template <typename R> void launch_strip_plan(const Dev<R> &S, cudaStream_t st);
+template <typename R> void launch_vlw_build(const Dev<R> &S, bool n3l, cudaStream_t st);
+template <typename R> void launch_vlw_force(const Dev<R> &S, const ljsel_config &cfg, int mode, bool ev,
+                                            int2 *pairs, long long pairs_cap, cudaStream_t st);
+void vlw_prepare();
 
 // Force evaluation.  mode: 0 forces into S.force (+ energy/virial if ev),
 // 1 forces fused with the Stormer-Verlet update (N3L off only), 2 export of

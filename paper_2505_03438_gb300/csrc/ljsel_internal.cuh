@@ -24,8 +24,19 @@ constexpr uint32_t JBITS = 27;
 constexpr uint32_t JMASK = (1u << JBITS) - 1u;
 
 __host__ __device__ inline uint32_t encode_image(int sx, int sy, int sz) {
-    int s = (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1);  // 13 = no image
-    return (uint32_t)((s + 14) % 27);
+    int s = (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1) + 14;  // 13 + 14 = 27 -> 0 = no image
+    return (uint32_t)(s >= 27 ? s - 27 : s);
+}
+
+// Neighbour cell coordinate c + o (|o| <= 2) wrapped into [0, n) with the
+// image coefficient s (x_j image = x_j + s L); returns false when the image
+// lies two box lengths away (only when n = 1 and |o| = 2).
+__host__ __device__ inline bool wrap_cell(int c, int o, int n, int &w, int &s) {
+    w = c + o;
+    s = 0;
+    if (w < 0) { w += n; s = -1; }
+    else if (w >= n) { w -= n; s = 1; }
+    return w >= 0 && w < n;
 }
 __host__ __device__ inline void decode_image(uint32_t c, int &sx, int &sy, int &sz) {
     int s = ((int)c + 13) % 27;
@@ -77,7 +88,7 @@ struct Ctrl {
     int32_t half_kick;         // next step kicks by dt/2 (velocities at integer time)
     int32_t rebuild_interval;
     int32_t loop_on;
-    int32_t pad0;
+    int32_t window_overflow;   // a cell's neighbourhood window exceeds its capacity
     int64_t steps_done;        // steps done by the current advance call
     int64_t steps_target;
     int64_t total_steps;
@@ -123,11 +134,21 @@ template <typename R> struct Dev {
     unsigned long long *tmp_key; // [n]
     int *cell_sorted;     // [n] cell of each sorted particle
     int *scan_partial;    // [nblocks] decoupled look-back state
-    // Verlet lists (ELL, column-major: entry k of row i at k*stride + i)
+    // Verlet lists, row-major: row i holds nl_cap entries at nl + i*nl_cap
+    // (nl_cap a multiple of 4).  Entries without a periodic image fill the
+    // row from the front, followed by entries naming the sentinel particle n
+    // up to a multiple of 4, so they are read as 16-byte chunks without
+    // bounds checks; entries with an image fill the row from the back.
+    // nl_count[i] = front count | (back count << 16).  pos[.][n] is a
+    // sentinel far outside the box.
     uint32_t *nl;
+    uint16_t *nl16;       // window lists (same buffer as nl, 16-bit entries)
     int *nl_count;
     int nl_cap;
-    int nl_stride;
+    // window strips: (row, x0, x1, -) per strip; *nstrips of them
+    int4 *strips;
+    int *nstrips;
+    int strip_cap;
     // clusters
     int M;                // cluster size
     int ncl_cap;
@@ -167,9 +188,11 @@ __device__ __forceinline__ double image_dx(double xi, double xj, int s, double L
 
 // The exact cutoff predicate on working positions promoted to double:
 // dx = x_i - (x_j + s L), r^2 = (dx*dx + dy*dy) + dz*dz with every product
-// and sum rounded separately, in range iff r^2 < r_c^2.
-static __device__ __noinline__ bool exact_in_range(double xi, double yi, double zi, double xj, double yj, double zj,
-                                            int sx, int sy, int sz, const double *boxd, double rc2d) {
+// and sum rounded separately, in range iff r^2 < r_c^2.  Out of line and
+// taking the FP32 values, so that the common path never pays for it.
+static __device__ __noinline__ bool exact_in_range(float fxi, float fyi, float fzi, float fxj, float fyj, float fzj,
+                                                   int sx, int sy, int sz, const double *boxd, double rc2d) {
+    const double xi = fxi, yi = fyi, zi = fzi, xj = fxj, yj = fyj, zj = fzj;
     double dx = __dsub_rn(xi, __dadd_rn(xj, (double)sx * boxd[0]));
     double dy = __dsub_rn(yi, __dadd_rn(yj, (double)sy * boxd[1]));
     double dz = __dsub_rn(zi, __dadd_rn(zj, (double)sz * boxd[2]));
@@ -197,9 +220,9 @@ template <typename R> struct Cut;
 template <> struct Cut<float> {
     __device__ __forceinline__ static bool in(float r2, float lo, float hi, const float4 &pi, const float4 &pj,
                                               int sx, int sy, int sz, const double *boxd, double rc2d) {
-        if (r2 < lo) return true;
-        if (!(r2 <= hi)) return false;
-        return exact_in_range(pi.x, pi.y, pi.z, pj.x, pj.y, pj.z, sx, sy, sz, boxd, rc2d);
+        bool in = r2 < lo;
+        if (!in && r2 <= hi) in = exact_in_range(pi.x, pi.y, pi.z, pj.x, pj.y, pj.z, sx, sy, sz, boxd, rc2d);
+        return in;
     }
 };
 template <> struct Cut<double> {

@@ -21,6 +21,7 @@ constexpr unsigned long long FLAG_A = 1ull << 62;  // tile aggregate published
 constexpr unsigned long long FLAG_P = 2ull << 62;  // inclusive prefix published
 constexpr unsigned long long VAL_MASK = (1ull << 62) - 1ull;
 constexpr int SPIN_LIMIT = 1 << 22;
+constexpr int VL_BUILD_THREADS = 128;
 
 __device__ __forceinline__ unsigned morton3(unsigned x, unsigned y, unsigned z) {
     unsigned k = 0;
@@ -28,15 +29,17 @@ __device__ __forceinline__ unsigned morton3(unsigned x, unsigned y, unsigned z) 
     return k;
 }
 
-__device__ __forceinline__ int floor_div(int a, int b) { int q = a / b; return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q; }
-
 template <typename R>
 __global__ void k_bin(Dev<R> S, int ntiles) {
     Ctrl *C = S.ctrl;
     if (!C->rebuild_now) return;
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p < ntiles) reinterpret_cast<unsigned long long *>(S.scan_partial)[p] = 0ull;
-    if (p == 0) C->need_cap = 0;
+    if (p == 0) {
+        C->need_cap = 0;
+        C->window_overflow = 0;
+        if (S.nstrips) *S.nstrips = 0;
+    }
     if (p >= S.n) return;
     const int sp = C->state_par;
     double *X = S.x[sp];
@@ -221,55 +224,134 @@ __global__ void k_sortgather(Dev<R> S) {
     }
 }
 
-// Verlet-list row of particle i (sorted index): all j in the stencil cells
-// with r^2 < r_list^2 (working precision), j != i; with N3L only j > i.
+// Verlet-list rows of the particles of one cell (one warp per cell, lane =
+// particle, 32 at a time): all j in the 27 stencil cells with r^2 < r_list^2
+// (working precision), j != i; with N3L only j > i.  For each of the 9
+// neighbouring (y, z) rows the three stencil cells cx-1, cx, cx+1 are one
+// run of consecutive sorted particles (split only at a periodic x edge), so
+// the whole warp walks 9 runs in lockstep with uniform-address loads, four
+// candidates at a time.  Entries without an image go to the front of the
+// row in 16-byte chunks of four, padded with the sentinel index n; entries
+// with an image go to the back, one by one.  The list test needs no exact
+// image arithmetic: the list radius carries a relative margin of 2^-12, far
+// above the rounding of a plain shift, so i is shifted once per run.
 template <typename R, bool N3L>
-__global__ void k_vl_build(Dev<R> S) {
+__global__ void __launch_bounds__(VL_BUILD_THREADS) k_vl_build(Dev<R> S) {
     Ctrl *C = S.ctrl;
     if (!C->rebuild_now) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= S.n) return;
-    const int pp = C->pos_par;
-    const V4<R> *P = S.pos[pp];
-    const V4<R> pi = P[i];
-    const int c = S.cell_sorted[i];
-    const int cx = c % S.nc[0], cy = (c / S.nc[0]) % S.nc[1], cz = c / (S.nc[0] * S.nc[1]);
-    int cnt = 0;
-    const int rch = S.reach;
-    for (int oz = -rch; oz <= rch; ++oz) {
-        int rz = cz + oz, sz = floor_div(rz, S.nc[2]);
-        if (sz < -1 || sz > 1) continue;
-        int wz = rz - sz * S.nc[2];
-        for (int oy = -rch; oy <= rch; ++oy) {
-            int ry = cy + oy, sy = floor_div(ry, S.nc[1]);
-            if (sy < -1 || sy > 1) continue;
-            int wy = ry - sy * S.nc[1];
-            for (int ox = -rch; ox <= rch; ++ox) {
-                int rx = cx + ox, sx = floor_div(rx, S.nc[0]);
-                if (sx < -1 || sx > 1) continue;
-                int wx = rx - sx * S.nc[0];
-                int cc = (wz * S.nc[1] + wy) * S.nc[0] + wx;
-                uint32_t code = encode_image(sx, sy, sz);
-                int jb = S.cell_start[cc], je = S.cell_start[cc + 1];
-                for (int j = jb; j < je; ++j) {
-                    if (j == i && code == 0) continue;
-                    if (N3L && j < i) continue;
-                    V4<R> pj = P[j];
-                    R dx = image_dx(pi.x, pj.x, sx, S.box[0], S.box_lo[0]);
-                    R dy = image_dx(pi.y, pj.y, sy, S.box[1], S.box_lo[1]);
-                    R dz = image_dx(pi.z, pj.z, sz, S.box[2], S.box_lo[2]);
-                    R r2 = r2_of(dx, dy, dz);
-                    if (r2 < S.rlist2) {
-                        if (cnt < S.nl_cap) S.nl[(size_t)cnt * S.nl_stride + i] = (uint32_t)j | (code << JBITS);
-                        ++cnt;
+    const int lane = threadIdx.x & 31;
+    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (c >= S.ncell) return;
+    const V4<R> *P = S.pos[C->pos_par];
+    const int nx = S.nc[0], ny = S.nc[1], nz = S.nc[2];
+    const int cxy = c % (nx * ny);
+    const int cx = cxy % nx, cy = cxy / nx, cz = c / (nx * ny);
+    const int cs = S.cell_start[c], ce = S.cell_start[c + 1];
+    const int cap = S.nl_cap;
+    for (int base = cs; base < ce; base += 32) {
+        const int i = base + lane;
+        const bool act = i < ce;
+        const V4<R> pi = P[act ? i : cs];
+        uint32_t *rowp = S.nl + (size_t)(act ? i : cs) * cap;
+        uint4 *row = reinterpret_cast<uint4 *>(rowp);
+        uint32_t b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+        int nf = 0, nb = 0;
+        // entries of the current chunk live in a 4-register shift queue and
+        // are stored as one 16-byte chunk when four have been found
+        auto accept = [&](int j, uint32_t code) {
+            if (code == 0) {
+                b3 = b2; b2 = b1; b1 = b0; b0 = (uint32_t)j;
+                ++nf;
+                if ((nf & 3) == 0 && nf + nb <= cap) row[(nf >> 2) - 1] = make_uint4(b0, b1, b2, b3);
+            } else {
+                if (nf + nb < cap && ((nf + 4) & ~3) + nb < cap) rowp[cap - 1 - nb] = (uint32_t)j | (code << JBITS);
+                ++nb;
+            }
+        };
+        for (int dz = N3L ? 0 : -1; dz <= 1; ++dz) {
+            int wz, sz;
+            wrap_cell(cz, dz, nz, wz, sz);
+            for (int dy = -1; dy <= 1; ++dy) {
+                // with N3L a geometric half stencil: rows dz = +1, row (0, +1),
+                // and in i's own row the cells cx (j > i only) and cx + 1
+                if (N3L && dz == 0 && dy < 0) continue;
+                const bool own_row = dz == 0 && dy == 0;
+                int wy, sy;
+                wrap_cell(cy, dy, ny, wy, sy);
+                const int rowc = (wz * ny + wy) * nx;
+                // runs: [left edge][middle][right edge], merged when contiguous
+                for (int seg = 0; seg < 3; ++seg) {
+                    int xa, xb, sx;  // cells [xa, xb] of this run, image sx
+                    if (N3L && own_row) {
+                        if (seg == 0) continue;  // no cx - 1
+                        if (seg == 1) { xa = xb = cx; sx = 0; }
+                        else {
+                            int w, s_;
+                            wrap_cell(cx, 1, nx, w, s_);
+                            xa = xb = w; sx = s_;
+                        }
+                    } else if (cx - 1 >= 0 && cx + 1 <= nx - 1) {
+                        if (seg > 0) break;
+                        xa = cx - 1; xb = cx + 1; sx = 0;
+                    } else if (seg == 0) {
+                        int w, s_;
+                        wrap_cell(cx, -1, nx, w, s_);
+                        xa = xb = w; sx = s_;
+                    } else if (seg == 1) {
+                        xa = xb = cx; sx = 0;
+                    } else {
+                        int w, s_;
+                        wrap_cell(cx, 1, nx, w, s_);
+                        xa = xb = w; sx = s_;
+                    }
+                    const uint32_t code = encode_image(sx, sy, sz);
+                    int jb = S.cell_start[rowc + xa], je = S.cell_start[rowc + xb + 1];
+                    // does this run contain i's own cell without an image?
+                    const bool self = code == 0 && jb <= cs && cs < je;
+                    const R xs = pi.x - (R)sx * S.box[0], ys = pi.y - (R)sy * S.box[1], zs = pi.z - (R)sz * S.box[2];
+                    int j = jb;
+                    for (; j + 4 <= je; j += 4) {
+                        const V4<R> q0 = ldpos(P, j), q1 = ldpos(P, j + 1), q2 = ldpos(P, j + 2), q3 = ldpos(P, j + 3);
+                        bool t0 = r2_of(xs - q0.x, ys - q0.y, zs - q0.z) < S.rlist2;
+                        bool t1 = r2_of(xs - q1.x, ys - q1.y, zs - q1.z) < S.rlist2;
+                        bool t2 = r2_of(xs - q2.x, ys - q2.y, zs - q2.z) < S.rlist2;
+                        bool t3 = r2_of(xs - q3.x, ys - q3.y, zs - q3.z) < S.rlist2;
+                        if (self) {
+                            if (N3L) { t0 = t0 && j > i; t1 = t1 && j + 1 > i; t2 = t2 && j + 2 > i; t3 = t3 && j + 3 > i; }
+                            else { t0 = t0 && j != i; t1 = t1 && j + 1 != i; t2 = t2 && j + 2 != i; t3 = t3 && j + 3 != i; }
+                        }
+                        if (act && (t0 | t1 | t2 | t3)) {
+                            if (t0) accept(j, code);
+                            if (t1) accept(j + 1, code);
+                            if (t2) accept(j + 2, code);
+                            if (t3) accept(j + 3, code);
+                        }
+                    }
+                    for (; j < je; ++j) {
+                        const V4<R> q = ldpos(P, j);
+                        bool t = r2_of(xs - q.x, ys - q.y, zs - q.z) < S.rlist2;
+                        if (self) t = t && (N3L ? j > i : j != i);
+                        if (act && t) accept(j, code);
                     }
                 }
             }
         }
+        if (act) {
+            const int need = ((nf + 3) & ~3) + nb;
+            if (need > cap || nb > 0xffff || nf > 0xffff) {
+                C->overflow = 1;
+                S.nl_count[i] = 0;
+            } else {
+                if (nf & 3) {  // sentinel padding of the last chunk
+                    const uint32_t sent = (uint32_t)S.n;
+                    for (int m = nf & 3; m < 4; ++m) { b3 = b2; b2 = b1; b1 = b0; b0 = sent; }
+                    row[nf >> 2] = make_uint4(b0, b1, b2, b3);
+                }
+                S.nl_count[i] = nf | (nb << 16);
+            }
+            atomicMax(reinterpret_cast<unsigned long long *>(&C->need_cap), (unsigned long long)need);
+        }
     }
-    S.nl_count[i] = cnt < S.nl_cap ? cnt : S.nl_cap;
-    if (cnt > S.nl_cap) C->overflow = 1;
-    atomicMax(reinterpret_cast<unsigned long long *>(&C->need_cap), (unsigned long long)cnt);
 }
 
 // Clusters: each cell's segment is cut into chunks of M consecutive sorted
@@ -331,17 +413,14 @@ __global__ void k_cp_build(Dev<R> S) {
     const int rch = S.reach;
     int cnt = 0;
     for (int oz = -rch; oz <= rch; ++oz) {
-        int rz = cz + oz, sz = floor_div(rz, S.nc[2]);
-        if (sz < -1 || sz > 1) continue;
-        int wz = rz - sz * S.nc[2];
+        int wz, sz;
+        if (!wrap_cell(cz, oz, S.nc[2], wz, sz)) continue;
         for (int oy = -rch; oy <= rch; ++oy) {
-            int ry = cy + oy, sy = floor_div(ry, S.nc[1]);
-            if (sy < -1 || sy > 1) continue;
-            int wy = ry - sy * S.nc[1];
+            int wy, sy;
+            if (!wrap_cell(cy, oy, S.nc[1], wy, sy)) continue;
             for (int ox = -rch; ox <= rch; ++ox) {
-                int rx = cx + ox, sx = floor_div(rx, S.nc[0]);
-                if (sx < -1 || sx > 1) continue;
-                int wx = rx - sx * S.nc[0];
+                int wx, sx;
+                if (!wrap_cell(cx, ox, S.nc[0], wx, sx)) continue;
                 int cc = (wz * S.nc[1] + wy) * S.nc[0] + wx;
                 uint32_t code = encode_image(sx, sy, sz);
                 int jb = S.clcell_start[cc], je = S.clcell_start[cc + 1];
@@ -405,8 +484,9 @@ template <typename R> void launch_sortgather(const Dev<R> &S, cudaStream_t st) {
     k_sortgather<R><<<div_up((long long)S.ncell * 32, 256), 256, 0, st>>>(S);
 }
 template <typename R> void launch_vl_build(const Dev<R> &S, bool n3l, cudaStream_t st) {
-    if (n3l) k_vl_build<R, true><<<div_up(S.n, 128), 128, 0, st>>>(S);
-    else k_vl_build<R, false><<<div_up(S.n, 128), 128, 0, st>>>(S);
+    const int blocks = div_up((long long)S.ncell * 32, VL_BUILD_THREADS);
+    if (n3l) k_vl_build<R, true><<<blocks, VL_BUILD_THREADS, 0, st>>>(S);
+    else k_vl_build<R, false><<<blocks, VL_BUILD_THREADS, 0, st>>>(S);
 }
 template <typename R> void launch_cluster_form(const Dev<R> &S, cudaStream_t st) {
     k_cluster_form<R><<<div_up(S.ncell, 128), 128, 0, st>>>(S);

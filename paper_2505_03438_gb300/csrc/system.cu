@@ -104,7 +104,7 @@ ljsel_status validate_params(const ljsel_params *p) {
 
 ljsel_status validate_config(const System &s, const ljsel_config *c) {
     if (!c) { set_error("config is NULL"); return LJSEL_ERR_ARG; }
-    if (c->method < 0 || c->method > 2) { set_error("unknown method"); return LJSEL_ERR_UNSUPPORTED; }
+    if (c->method < 0 || c->method > 3) { set_error("unknown method"); return LJSEL_ERR_UNSUPPORTED; }
     if (c->rebuild_interval < 1) { set_error("rebuild_interval must be >= 1"); return LJSEL_ERR_ARG; }
     if (c->csf != 1.0 && c->csf != 0.5) { set_error("csf must be 1.0 or 0.5"); return LJSEL_ERR_UNSUPPORTED; }
     if (c->newton3 != 0 && c->newton3 != 1) { set_error("newton3 must be 0 or 1"); return LJSEL_ERR_ARG; }
@@ -116,6 +116,9 @@ ljsel_status validate_config(const System &s, const ljsel_config *c) {
         if (M != 4 && M != 8 && M != 32) { set_error("cluster_size must be 4, 8 or 32"); return LJSEL_ERR_UNSUPPORTED; }
         if (t < M || t > 32 || (t & (t - 1)) != 0) { set_error("CLUSTER threads_per_unit must be M, 2M, ... <= 32"); return LJSEL_ERR_UNSUPPORTED; }
         if (c->newton3 && t != M) { set_error("CLUSTER with N3L uses threads_per_unit = M"); return LJSEL_ERR_UNSUPPORTED; }
+    } else if (c->method == LJSEL_METHOD_VLW) {
+        if (t != 1) { set_error("VLW uses threads_per_unit = 1"); return LJSEL_ERR_UNSUPPORTED; }
+        if (c->csf != 1.0) { set_error("VLW uses csf = 1"); return LJSEL_ERR_UNSUPPORTED; }
     } else {
         if (t != 1) { set_error("LC uses threads_per_unit = 1"); return LJSEL_ERR_UNSUPPORTED; }
     }
@@ -140,7 +143,7 @@ System::~System() {
 std::vector<Buf *> System::all_bufs() {
     return {&b_x[0], &b_x[1], &b_v[0], &b_v[1], &b_id[0], &b_id[1], &b_type[0], &b_type[1], &b_pos[0], &b_pos[1],
             &b_xref, &b_force, &b_cell_count, &b_cell_start, &b_clcell_start, &b_cell_of, &b_slot_of, &b_key_of,
-            &b_tmp_idx, &b_tmp_key, &b_cell_sorted, &b_scan, &b_nl, &b_nl_count, &b_cl_first, &b_cl_count,
+            &b_tmp_idx, &b_tmp_key, &b_cell_sorted, &b_scan, &b_nl, &b_nl_count, &b_strips, &b_nstrips, &b_cl_first, &b_cl_count,
             &b_cl_cell, &b_cl_lo, &b_cl_hi, &b_cp, &b_cp_count, &b_ncl, &b_ctrl, &b_io};
 }
 
@@ -176,7 +179,7 @@ ljsel_status System::alloc_base() {
         LJ_TRY(b_v[k].ensure(n3));
         LJ_TRY(b_id[k].ensure((size_t)n * 4));
         LJ_TRY(b_type[k].ensure((size_t)n * 4));
-        LJ_TRY(b_pos[k].ensure((size_t)n * p4()));
+        LJ_TRY(b_pos[k].ensure((size_t)(n + 1) * p4()));
     }
     LJ_TRY(b_xref.ensure((size_t)n * p4()));
     LJ_TRY(b_force.ensure((size_t)n * p4()));
@@ -191,6 +194,18 @@ ljsel_status System::alloc_base() {
     LJ_CUDA(cudaMemsetAsync(b_ncl.ptr, 0, 16, stream));
     LJ_TRY(b_ctrl.ensure(sizeof(Ctrl)));
     LJ_CUDA(cudaMemsetAsync(b_ctrl.ptr, 0, sizeof(Ctrl), stream));
+    // the sentinel particle n that pads list rows: far outside the box, so
+    // every pair with it is out of range and its force term is exactly zero
+    for (int k = 0; k < 2; ++k) {
+        if (precision) {
+            D4 far = {1e18, 1e18, 1e18, 0.0};
+            LJ_CUDA(cudaMemcpyAsync((char *)b_pos[k].ptr + (size_t)n * p4(), &far, sizeof(far), cudaMemcpyHostToDevice, stream));
+        } else {
+            float4 far = make_float4(1e18f, 1e18f, 1e18f, 0.f);
+            LJ_CUDA(cudaMemcpyAsync((char *)b_pos[k].ptr + (size_t)n * p4(), &far, sizeof(far), cudaMemcpyHostToDevice, stream));
+        }
+    }
+    LJ_CUDA(cudaStreamSynchronize(stream));
     return LJSEL_OK;
 }
 
@@ -224,9 +239,24 @@ ljsel_status System::apply_config() {
             if (cfg.newton3) est = est * 0.5 + 8;
             nl_cap = (int)std::min(est, 4096.0);
         }
-        nl_stride = ((n + 31) / 32) * 32;
-        LJ_TRY(grow(b_nl, (size_t)nl_cap * nl_stride * 4));
-        LJ_TRY(grow(b_nl_count, (size_t)nl_stride * 4));
+        nl_cap = (nl_cap + 3) & ~3;
+        LJ_TRY(grow(b_nl, (size_t)nl_cap * n * 4));
+        LJ_TRY(grow(b_nl_count, (size_t)n * 4));
+    }
+    if (cfg.method == LJSEL_METHOD_VLW) {
+        vlw_prepare();
+        if (nl_cap <= 0) {
+            const double vol = params.box[0] * params.box[1] * params.box[2];
+            const double rho = n / vol;
+            double est = 4.18879 * rlist * rlist * rlist * rho * 1.35 + 24;
+            if (cfg.newton3) est = est * 0.5 + 16;
+            nl_cap = (int)std::min(est, 4096.0);
+        }
+        nl_cap = std::min((nl_cap + 15) & ~15, 512);  // two half-rows, at most 255 + 1 entries each
+        LJ_TRY(grow(b_nl, (size_t)nl_cap * n * 2));
+        LJ_TRY(grow(b_nl_count, (size_t)n * 4));
+        LJ_TRY(grow(b_strips, (size_t)ncell * sizeof(int4)));
+        LJ_TRY(grow(b_nstrips, 16));
     }
     if (cfg.method == LJSEL_METHOD_CLUSTER) {
         ncl_cap = n / M + ncell + 1;
@@ -289,9 +319,12 @@ template <typename R> void System::fill_dev(Dev<R> &S) const {
     S.cell_sorted = (int *)b_cell_sorted.ptr;
     S.scan_partial = (int *)b_scan.ptr;
     S.nl = (uint32_t *)b_nl.ptr;
+    S.nl16 = (uint16_t *)b_nl.ptr;
+    S.strips = (int4 *)b_strips.ptr;
+    S.nstrips = (int *)b_nstrips.ptr;
+    S.strip_cap = ncell;
     S.nl_count = (int *)b_nl_count.ptr;
     S.nl_cap = nl_cap;
-    S.nl_stride = nl_stride;
     S.M = M;
     S.ncl_cap = ncl_cap;
     S.cl_first = (int *)b_cl_first.ptr;
@@ -359,6 +392,10 @@ ljsel_status System::read_ctrl() {
 ljsel_status System::check_device_errors() {
     if (h_ctrl->nonfinite) { set_error("non-finite position, velocity or force"); return LJSEL_ERR_NONFINITE; }
     if (h_ctrl->timeout) { set_error("a bounded device wait gave up (scan look-back)"); return LJSEL_ERR_TIMEOUT; }
+    if (h_ctrl->window_overflow) {
+        set_error("a cell's neighbourhood window holds more than 2047 particles: VLW is not available here");
+        return LJSEL_ERR_UNSUPPORTED;
+    }
     return LJSEL_OK;
 }
 
@@ -368,6 +405,10 @@ template <typename R> void System::enqueue_rebuild(const Dev<R> &S, cudaStream_t
     launch_scatter(S, st);
     launch_sortgather(S, st);
     if (cfg.method == LJSEL_METHOD_VL) launch_vl_build(S, cfg.newton3 != 0, st);
+    if (cfg.method == LJSEL_METHOD_VLW) {
+        launch_strip_plan(S, st);
+        launch_vlw_build(S, cfg.newton3 != 0, st);
+    }
     if (cfg.method == LJSEL_METHOD_CLUSTER) {
         launch_cluster_form(S, st);
         launch_cp_build(S, cfg.newton3 != 0, st);
@@ -389,7 +430,11 @@ template <typename R> void System::enqueue_step(const Dev<R> &S, bool ev, cudaSt
 ljsel_status System::handle_overflow() {
     const long long need = h_ctrl->need_cap;
     const long long cap = (long long)std::max<long long>(need + need / 5 + 8, 16);
-    if (cfg.method == LJSEL_METHOD_VL) nl_cap = (int)cap;
+    if (cfg.method == LJSEL_METHOD_VL) nl_cap = (int)((cap + 3) & ~3LL);
+    else if (cfg.method == LJSEL_METHOD_VLW) {
+        if (cap > 512) { set_error("VLW rows hold at most 510 entries; the system is too dense for VLW"); return LJSEL_ERR_UNSUPPORTED; }
+        nl_cap = (int)((cap + 15) & ~15LL);
+    }
     else if (cfg.method == LJSEL_METHOD_CLUSTER) cp_cap = (int)cap;
     capacity_retries += 1;
     if (capacity_retries > 64) { set_error("neighbour list keeps overflowing"); return LJSEL_ERR_CAPACITY; }
@@ -538,7 +583,8 @@ template <typename R> ljsel_status System::profile(long long nsteps, ljsel_profi
     auto done = [&]() { for (auto &e : ev) cudaEventDestroy(e); };
     Dev<R> S;
     fill_dev(S);
-    const int chain = 5 + (cfg.method == LJSEL_METHOD_VL ? 1 : 0) + (cfg.method == LJSEL_METHOD_CLUSTER ? 2 : 0);
+    const int chain = 5 + (cfg.method == LJSEL_METHOD_VL ? 1 : 0) + (cfg.method == LJSEL_METHOD_CLUSTER ? 2 : 0) +
+                      (cfg.method == LJSEL_METHOD_VLW ? 2 : 0);
     LJ_TRY(cmd(CMD_BEGIN, nsteps));
     double tr = 0, tf = 0, tu = 0, tc = 0;
     for (long long k = 0; k < nsteps; ++k) {

@@ -44,7 +44,7 @@ struct System {
     double rlist = 0;
     int M = 1;
     // list capacities
-    int nl_cap = 0, nl_stride = 0;
+    int nl_cap = 0;
     int ncl_cap = 0, cp_cap = 0, cp_stride = 0;
     long long capacity_retries = 0;
     bool structure_dirty = true;
@@ -54,7 +54,7 @@ struct System {
     Buf b_xref, b_force;
     Buf b_cell_count, b_cell_start, b_clcell_start, b_cell_of, b_slot_of, b_key_of, b_tmp_idx, b_tmp_key,
         b_cell_sorted, b_scan;
-    Buf b_nl, b_nl_count;
+    Buf b_nl, b_nl_count, b_strips, b_nstrips;
     Buf b_cl_first, b_cl_count, b_cl_cell, b_cl_lo, b_cl_hi, b_cp, b_cp_count, b_ncl;
     Buf b_ctrl, b_io;
     Ctrl *h_ctrl = nullptr;  // pinned mirror

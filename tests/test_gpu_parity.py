@@ -38,6 +38,8 @@ CONFIGS = [
     dict(method="VL", newton3=False, threads_per_unit=4),
     dict(method="VL", newton3=True, threads_per_unit=1),
     dict(method="VL", newton3=True, threads_per_unit=4),
+    dict(method="VLW", newton3=False),
+    dict(method="VLW", newton3=True),
     dict(method="CL", cluster_size=4, newton3=False, threads_per_unit=4),
     dict(method="CL", cluster_size=4, newton3=False, threads_per_unit=16),
     dict(method="CL", cluster_size=4, newton3=True, threads_per_unit=4),
@@ -134,7 +136,7 @@ def test_fp64_trajectory_small_fcc(lj):
     s.close()
 
 
-@pytest.mark.parametrize("method", ["VL", "LC", "CL"])
+@pytest.mark.parametrize("method", ["VL", "LC", "CL", "VLW"])
 def test_fp32_trajectory_tracks_fp64(lj, method):
     sc = scenarios.fcc_liquid(8, seed=21, jitter=0.05)
     s = lj.System(sc)
@@ -265,8 +267,9 @@ def test_liquid_1m_full_size(lj):
     """Full-size homogeneous liquid (N = 1,048,576) in the benchmark's launch
     configuration: whole pair set and all forces against the oracle."""
     sc = scenarios.liquid_1m()
-    s = lj.System(sc)
-    s.set_config(method="VL", rebuild_interval=10)
-    s.step(20)
-    check_against_oracle(s, sc)
-    s.close()
+    for cfg in (dict(method="VL"), dict(method="VLW"), dict(method="VLW", newton3=True)):
+        s = lj.System(sc)
+        s.set_config(rebuild_interval=10, **cfg)
+        s.step(20)
+        check_against_oracle(s, sc)
+        s.close()
