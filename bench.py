@@ -158,44 +158,66 @@ def run_ours(args):
     x = torch.tensor(sc["x"], device="cuda")
     v = torch.tensor(sc["v"], device="cuda")
     t = torch.zeros(n, dtype=torch.int32, device="cuda")
-    params = lj.make_params(sc["box"], skin=sc["skin"], dt=sc["dt"])
-    h = lj.ljsel_create(params, n, x, v, t, stream.cuda_stream)
-    if args.method:
-        lj.ljsel_set_config(h, lj.make_config(args.method, cluster_size=args.cluster, newton3=args.newton3,
-                                              threads_per_unit=args.tpu, rebuild_interval=sc["rebuild"]))
-    lj.ljsel_step(h, W)  # warm-up
-    torch.cuda.synchronize()
+    params = lj.make_params(sc["box"], skin=sc["skin"], dt=sc["dt"], use_graphs=not args.eager)
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    # ---- timed region: one tuning phase + the rest of the K steps ----------
+    def fresh():
+        hh = lj.ljsel_create(params, n, x, v, t, stream.cuda_stream)
+        if args.method:
+            lj.ljsel_set_config(hh, lj.make_config(args.method, cluster_size=args.cluster, newton3=args.newton3,
+                                                   threads_per_unit=args.tpu, rebuild_interval=sc["rebuild"]))
+        lj.ljsel_step(hh, W)  # warm-up
+        torch.cuda.synchronize()
+        return hh
+
+    def timed(hh, strategy):
+        """Timed region: one tuning phase (its trial steps count) + the rest of
+        the K steps, bracketed by a barrier and device synchronisation."""
+        c0 = lj.ljsel_get_counters(hh)
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rep = None
+        if strategy:
+            chosen, rep = lj.ljsel_autotune(hh, strategy=strategy, trial_steps=args.trial_steps,
+                                            probe_steps=args.probe_steps, probe_factor=2.0)
+            done = rep["trial_steps_total"]
+        else:
+            chosen, done = lj.ljsel_get_config(hh), 0
+        lj.ljsel_step(hh, max(0, K - done))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        c1 = lj.ljsel_get_counters(hh)
+        if dist is not None:
+            tt = torch.tensor([ms], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt.item())
+        steps = c1["steps"] - c0["steps"]
+        return {"ms": ms, "steps": steps, "chosen": chosen, "rep": rep,
+                "rebuilds": c1["rebuilds"] - c0["rebuilds"], "early": c1["early_rebuilds"] - c0["early_rebuilds"]}
+
+    headline = args.strategy if args.tune else None
+    other = [st for st in ("expert", "full") if args.tune and args.other and st != headline]
+    # the other strategy first, so the headline run is the last before profiling
+    extra_runs = {}
+    for st in other:
+        hx = fresh()
+        r = timed(hx, st)
+        extra_runs[st] = {"value": world * n * r["steps"] / (r["ms"] * 1e-3), "chosen": r["chosen"].name(),
+                          "tuner": r["rep"]}
+        lj.ljsel_destroy(hx)
+    h = fresh()
     clk = Clocks(local)
-    c0 = lj.ljsel_get_counters(h)
-    barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    rep = None
-    if args.tune:
-        chosen, rep = lj.ljsel_autotune(h, strategy=0, trial_steps=args.trial_steps)
-        done = rep["trial_steps_total"]
-    else:
-        chosen, done = lj.ljsel_get_config(h), 0
-    lj.ljsel_step(h, max(0, K - done))
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
+    run = timed(h, headline)
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1)
-    c1 = lj.ljsel_get_counters(h)
-    steps_done = c1["steps"] - c0["steps"]
-    if dist is not None:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms, steps_done, chosen, rep = run["ms"], run["steps"], run["chosen"], run["rep"]
     value = world * n * steps_done / (ms * 1e-3)
     chosen_name = chosen.name()
 
@@ -204,21 +226,26 @@ def run_ours(args):
     _, npairs = lj.ljsel_get_pairs(h, 0)
     cnt = lj.ljsel_get_counters(h)
 
-    # ---- every fixed configuration, same workload -------------------------
+    # ---- every fixed configuration, same workload: from the same initial
+    # state, the same warm-up, the same K timed steps ----------------------
     fixed = {}
-    if args.fixed_steps > 0:
+    if args.fixed_steps != 0:
+        kf = K if args.fixed_steps < 0 else args.fixed_steps
         for c in lj.ljsel_default_candidates(h):
+            lj.ljsel_set_state(h, x, v)
             lj.ljsel_set_config(h, c)
-            lj.ljsel_step(h, 10)
+            try:
+                lj.ljsel_step(h, W)
+            except lj.LjselError:
+                continue  # not available for this system
             torch.cuda.synchronize()
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            lj.ljsel_step(h, args.fixed_steps)
+            lj.ljsel_step(h, kf)
             b.record(stream)
             torch.cuda.synchronize()
-            fixed[c.name()] = n * args.fixed_steps / (a.elapsed_time(b) * 1e-3)
-        lj.ljsel_set_config(h, chosen)
+            fixed[c.name()] = n * kf / (a.elapsed_time(b) * 1e-3)
     lj.ljsel_destroy(h)
 
     # ---- end to end through the C ABI with host buffers -------------------
@@ -232,11 +259,12 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
-        hp = lj.make_params(sc["box"], skin=sc["skin"], dt=sc["dt"])
+        hp = lj.make_params(sc["box"], skin=sc["skin"], dt=sc["dt"], use_graphs=not args.eager)
         h2 = lj.ljsel_create(hp, n, xh, vh, th, stream.cuda_stream)
         done2 = 0
         if args.tune:
-            _, r2 = lj.ljsel_autotune(h2, strategy=0, trial_steps=args.trial_steps)
+            _, r2 = lj.ljsel_autotune(h2, strategy=args.strategy, trial_steps=args.trial_steps,
+                                      probe_steps=args.probe_steps, probe_factor=2.0)
             done2 = r2["trial_steps_total"]
         lj.ljsel_step(h2, max(0, K - done2))
         lj.ljsel_get_state(h2, xo, vo)
@@ -284,8 +312,9 @@ def run_ours(args):
         "gpu_launches": None,
         "kernel_ms": {k: prof[k] for k in ("rebuild_ms", "force_ms", "update_ms", "control_ms")},
         "pairs_within_cutoff": npairs,
-        "rebuilds": c1["rebuilds"] - c0["rebuilds"], "early_rebuilds": c1["early_rebuilds"] - c0["early_rebuilds"],
-        "tuner": rep,
+        "rebuilds": run["rebuilds"], "early_rebuilds": run["early"],
+        "tuner": dict(rep, strategy=headline) if rep else None,
+        "other_tuned_runs": extra_runs,
         "fixed": fixed,
         "best_fixed": max(fixed.items(), key=lambda kv: kv[1]) if fixed else None,
     }
@@ -294,7 +323,7 @@ def run_ours(args):
     # per-call loop-init and command kernels
     n3 = 1 if chosen.newton3 else 0
     chain = 5 + {lj.METHOD_VL: 1, lj.METHOD_CLUSTER: 2, lj.METHOD_VLW: 2}.get(chosen.method, 0)
-    line["gpu_launches"] = int(steps_done * (2 + n3) + (c1["rebuilds"] - c0["rebuilds"]) * chain)
+    line["gpu_launches"] = int(steps_done * (2 + n3) + run["rebuilds"] * chain)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -312,9 +341,14 @@ def main():
     ap.add_argument("--tpu", type=int, default=1)
     ap.add_argument("--cluster", type=int, default=8)
     ap.add_argument("--trial-steps", type=int, default=10)
-    ap.add_argument("--fixed-steps", type=int, default=200)
+    ap.add_argument("--probe-steps", type=int, default=2)
+    ap.add_argument("--strategy", default="expert", choices=["full", "predictive", "expert"],
+                    help="tuning strategy of the headline run (the other of expert/full is reported beside it)")
+    ap.add_argument("--fixed-steps", type=int, default=-1, help="steps per fixed configuration (-1: same as --steps)")
     ap.add_argument("--profile-steps", type=int, default=60)
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--eager", action="store_true", help="plain stream launches instead of the step graph")
+    ap.add_argument("--no-other", dest="other", action="store_false", help="skip the second tuning strategy")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -127,9 +127,12 @@ typedef struct ljsel_counters {
     int64_t capacity_retries;  /* list reallocations after an overflow         */
 } ljsel_counters;
 
-/* Autotuner options (Sec. 2.2.5 Full Search, Sec. 5.1 Predictive).       */
+/* Autotuner options (Sec. 2.2.5 Full Search, Sec. 5.1 Predictive, Sec. 5.2
+ * Expert).                                                                */
 typedef struct ljsel_tuner_opts {
-    int32_t strategy;          /* 0: full search; 1: predictive              */
+    int32_t strategy;          /* 0: full search; 1: predictive; 2: expert
+                                  (fuzzy rules on the mean particles per
+                                  CSF-1 bin, Sec. 4 statistics)               */
     int32_t trial_steps;       /* steps per trial (>= 1); a trial first
                                   rebuilds, then advances trial_steps steps   */
     double predict_factor;     /* predictive: trial configs predicted within
@@ -140,6 +143,12 @@ typedef struct ljsel_tuner_opts {
                                   for this many phases (>= 1)                 */
     int32_t ncandidates;       /* > 0: use candidates[]; 0: the default set   */
     const ljsel_config *candidates;
+    int32_t probe_steps;       /* a trial first runs this many steps; when its
+                                  cost is above probe_factor x the best cost
+                                  of the phase so far, the trial stops there
+                                  (0: always run trial_steps)                 */
+    int32_t reserved;
+    double probe_factor;       /* e.g. 2.0                                     */
 } ljsel_tuner_opts;
 
 /* Result of the last tuning phase.                                        */
@@ -152,6 +161,9 @@ typedef struct ljsel_tuner_report {
     double phase_ms;           /* wall time of the last phase (all trials)    */
     double overhead_ms;        /* sum over trials of (trial - chosen) cost    */
     int64_t trial_steps_total; /* steps advanced by trials in the last phase  */
+    int32_t nprobed_out;       /* trials stopped after their probe            */
+    int32_t reserved;
+    double expert_input;       /* expert: mean particles per CSF-1 bin        */
 } ljsel_tuner_report;
 
 /* GPU time per kernel class, measured with CUDA events around each launch

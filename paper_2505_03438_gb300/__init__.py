@@ -90,6 +90,9 @@ class ljsel_tuner_opts(ctypes.Structure):
         ("retrial_phases", ctypes.c_int32),
         ("ncandidates", ctypes.c_int32),
         ("candidates", ctypes.POINTER(ljsel_config)),
+        ("probe_steps", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("probe_factor", ctypes.c_double),
     ]
 
 
@@ -103,6 +106,9 @@ class ljsel_tuner_report(ctypes.Structure):
         ("phase_ms", ctypes.c_double),
         ("overhead_ms", ctypes.c_double),
         ("trial_steps_total", ctypes.c_int64),
+        ("nprobed_out", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("expert_input", ctypes.c_double),
     ]
 
 
@@ -347,9 +353,11 @@ def ljsel_default_candidates(h):
 
 
 def ljsel_autotune(h, strategy=0, trial_steps=10, predict_factor=2.0, blacklist_factor=10.0, retrial_phases=4,
-                   candidates=None):
+                   candidates=None, probe_steps=0, probe_factor=2.0):
     o = ljsel_tuner_opts()
-    o.strategy = int(strategy)
+    o.strategy = {"full": 0, "predictive": 1, "expert": 2}.get(strategy, strategy)
+    o.probe_steps = int(probe_steps)
+    o.probe_factor = float(probe_factor)
     o.trial_steps = int(trial_steps)
     o.predict_factor = float(predict_factor)
     o.blacklist_factor = float(blacklist_factor)

@@ -462,20 +462,76 @@ ljsel_status ljsel_default_candidates(ljsel_system h, int32_t cap, ljsel_config 
     return LJSEL_OK;
 }
 
-// One tuning phase.  Each trialled configuration is selected, its neighbour
-// structure is built (timed), then opts->trial_steps steps are advanced
+// ---------------------------------------------------------------------------
+// Expert strategy (Sec. 5.2): a fuzzy system whose single input is the mean
+// number of particles per CSF-1 cell bin (a Sec. 4 statistic) rates each
+// configuration family Good / Okay / Bad; the crisp suitability is the
+// centre of gravity of the aggregated output set (Sec. 2.3), and only
+// configurations rated at least 0.5 are trialled.  The paper's rule file is
+// not available; these rules are ours, written from full searches of this
+// library: in a dense liquid (about 18 particles per bin) Verlet lists with
+// or without N3L are fastest, linked cells about 2x and the window and
+// cluster lists 1.5-3x slower; in a dilute gas the neighbour counts vanish
+// and linked cells, which build no list, are expected to win.
+struct Trap {
+    double a, b, c, d;  // 0 below a, rising to 1 at b, 1 until c, 0 from d
+    double operator()(double x) const {
+        if (x < a || x > d) return 0.0;
+        if (x < b) return b > a ? (x - a) / (b - a) : 1.0;
+        if (x <= c) return 1.0;
+        return d > c ? (d - x) / (d - c) : 1.0;
+    }
+};
+static const double INF = 1e300;
+static const Trap IN_SPARSE = {-INF, -INF, 1.0, 4.0}, IN_MEDIUM = {1.0, 4.0, 8.0, 12.0}, IN_DENSE = {8.0, 12.0, INF, INF};
+static const Trap OUT_BAD = {-INF, -INF, 0.1, 0.4}, OUT_OKAY = {0.2, 0.5, 0.5, 0.8}, OUT_GOOD = {0.6, 0.9, INF, INF};
+
+// consequent term per (family, input term): 0 bad, 1 okay, 2 good
+static int expert_rule(const ljsel_config &c, int input_term) {
+    static const int VL_[3] = {1, 2, 2}, VLW_[3] = {0, 1, 1}, LC_[3] = {2, 1, 0}, CL_[3] = {1, 0, 0};
+    switch (c.method) {
+        case LJSEL_METHOD_VL: return VL_[input_term];
+        case LJSEL_METHOD_VLW: return VLW_[input_term];
+        case LJSEL_METHOD_LC: return LC_[input_term];
+        default: return CL_[input_term];
+    }
+}
+
+static double expert_suitability(const ljsel_config &c, double mean_per_bin) {
+    const double w[3] = {IN_SPARSE(mean_per_bin), IN_MEDIUM(mean_per_bin), IN_DENSE(mean_per_bin)};
+    const Trap *out[3] = {&OUT_BAD, &OUT_OKAY, &OUT_GOOD};
+    double num = 0.0, den = 0.0;
+    for (int k = 0; k <= 200; ++k) {
+        const double y = k / 200.0;
+        double m = 0.0;
+        for (int t = 0; t < 3; ++t) m = std::max(m, std::min(w[t], (*out[expert_rule(c, t)])(y)));
+        num += m * y;
+        den += m;
+    }
+    return den > 0 ? num / den : 0.0;
+}
+
+// One tuning phase.  Candidates are trialled in the order of their last
+// measured cost.  Each trial selects the configuration, builds its
+// neighbour structure (timed), then advances opts->trial_steps steps
 // (timed); cost per step = build time / R + step time / trial_steps, the
-// weighted average of build and force time of Sec. 2.2.5.  Trials advance
-// the simulation (Sec. 1).  Predictive strategy (Sec. 5.1): after two phases
-// a config is trialled only if its cost, extrapolated linearly from its last
-// two measurements, is within predict_factor of the best prediction, or if
-// it has not been trialled for retrial_phases phases; configs measured
-// slower than blacklist_factor x the best are dropped for good.
+// weighted average of build and force time of Sec. 2.2.5.  Trials advance the
+// simulation (Sec. 1).  With probe_steps > 0 a trial whose first probe_steps
+// steps already cost more than probe_factor x the best cost of the phase
+// stops there.  Predictive strategy (Sec. 5.1): after two phases a config is
+// trialled only if its cost, extrapolated linearly from its last two
+// measurements, is within predict_factor of the best prediction, or if it
+// has not been trialled for retrial_phases phases; configs measured slower
+// than blacklist_factor x the best are dropped for good.  Expert strategy:
+// see expert_suitability.
 ljsel_status ljsel_autotune(ljsel_system h, const ljsel_tuner_opts *opts, ljsel_config *chosen,
                             ljsel_tuner_report *report) {
     System *s = (System *)h;
     if (!s || !opts) { set_error("NULL argument"); return LJSEL_ERR_ARG; }
-    if (opts->trial_steps < 1 || (opts->strategy != 0 && opts->strategy != 1)) { set_error("invalid tuner options"); return LJSEL_ERR_ARG; }
+    if (opts->trial_steps < 1 || opts->strategy < 0 || opts->strategy > 2 || opts->probe_steps < 0) {
+        set_error("invalid tuner options");
+        return LJSEL_ERR_ARG;
+    }
     auto t0 = std::chrono::steady_clock::now();
     std::vector<ljsel_config> cands;
     if (opts->ncandidates > 0) {
@@ -487,25 +543,31 @@ ljsel_status ljsel_autotune(ljsel_system h, const ljsel_tuner_opts *opts, ljsel_
     } else {
         cands = default_candidates(*s);
     }
-    // (re)attach persistent per-candidate state
-    std::vector<TunerEntry *> ent;
     for (const ljsel_config &c : cands) {
-        TunerEntry *found = nullptr;
-        for (TunerEntry &e : s->tuner)
-            if (same_cfg(e.cfg, c)) found = &e;
-        if (!found) {
-            s->tuner.push_back(TunerEntry{c, {}, -1, false});
-            found = nullptr;
-        }
-        ent.push_back(found);
+        bool found = false;
+        for (TunerEntry &e : s->tuner) found = found || same_cfg(e.cfg, c);
+        if (!found) s->tuner.push_back(TunerEntry{c, {}, -1, false});
     }
+    std::vector<TunerEntry *> ent(cands.size(), nullptr);
     for (size_t k = 0; k < cands.size(); ++k)
         for (TunerEntry &e : s->tuner)
             if (same_cfg(e.cfg, cands[k])) ent[k] = &e;
     const int phase = s->tuner_phase;
     // which candidates to trial
     std::vector<char> trial(cands.size(), 1);
-    if (opts->strategy == 1 && phase >= 2) {
+    double expert_x = -1.0;
+    if (opts->strategy == 2) {
+        ljsel_stats st;
+        TRY(ljsel_get_stats(h, &st));
+        expert_x = st.mean;
+        int any = 0;
+        for (size_t k = 0; k < cands.size(); ++k) {
+            trial[k] = !ent[k]->blacklisted && expert_suitability(cands[k], st.mean) >= 0.5;
+            any += trial[k];
+        }
+        if (!any)
+            for (size_t k = 0; k < cands.size(); ++k) trial[k] = !ent[k]->blacklisted;
+    } else if (opts->strategy == 1 && phase >= 2) {
         std::vector<double> pred(cands.size(), -1.0);
         double best = 1e300;
         for (size_t k = 0; k < cands.size(); ++k) {
@@ -532,54 +594,85 @@ ljsel_status ljsel_autotune(ljsel_system h, const ljsel_tuner_opts *opts, ljsel_
     } else {
         for (size_t k = 0; k < cands.size(); ++k) trial[k] = !ent[k]->blacklisted;
     }
+    // trial order: last measured cost ascending, unmeasured ones in set order
+    std::vector<size_t> order(cands.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+        const bool hx = !ent[x]->history.empty(), hy = !ent[y]->history.empty();
+        if (hx != hy) return hx;
+        if (!hx) return false;
+        return ent[x]->history.back().second < ent[y]->history.back().second;
+    });
     std::vector<double> cost(cands.size(), -1.0);
+    std::vector<char> probed_out(cands.size(), 0);
     int best_k = -1;
     long long steps_total = 0;
-    for (size_t k = 0; k < cands.size(); ++k) {
+    for (size_t oi = 0; oi < order.size(); ++oi) {
+        const size_t k = order[oi];
         if (!trial[k]) continue;
-        TRY(ljsel_set_config(h, &cands[k]));
+        ljsel_status sc = ljsel_set_config(h, &cands[k]);
+        if (sc == LJSEL_ERR_UNSUPPORTED) { ent[k]->blacklisted = true; continue; }
+        TRY(sc);
+        int done_steps = 0;
         ljsel_status st = dispatch(s, [&](auto z) -> ljsel_status {
             using R = decltype(z);
-            // timed build
+            float tb = 0, tp = 0, tr = 0, te = 0;
+            // timed build (ensure_structure synchronizes; subtract one empty round trip)
             CK(cudaEventRecord(s->ev_a, s->stream));
             TRY(s->ensure_structure<R>());
-            float tb = 0, ts = 0;
-            // ensure_structure synchronized the stream, so ev_b is complete
             CK(cudaEventRecord(s->ev_b, s->stream));
             CK(cudaEventSynchronize(s->ev_b));
             CK(cudaEventElapsedTime(&tb, s->ev_a, s->ev_b));
-            // the build time includes one host round trip; subtract an empty one
             CK(cudaEventRecord(s->ev_a, s->stream));
             TRY(s->read_ctrl());
             CK(cudaEventRecord(s->ev_b, s->stream));
             CK(cudaEventSynchronize(s->ev_b));
-            float te = 0;
             CK(cudaEventElapsedTime(&te, s->ev_a, s->ev_b));
             tb = std::max(0.f, tb - te);
-            if (s->params.use_graphs && !s->gexec) TRY(s->build_graph<R>());
+            // trials use plain stream launches: instantiating a step graph
+            // per candidate would cost more than the trial itself
+            const int R_ = std::max(1, cands[k].rebuild_interval);
+            int probe = opts->probe_steps > 0 ? std::min(opts->probe_steps, opts->trial_steps) : opts->trial_steps;
             CK(cudaEventRecord(s->ev_a, s->stream));
-            TRY(s->advance<R>(opts->trial_steps));
+            TRY(s->advance<R>(probe, true));
             CK(cudaEventRecord(s->ev_b, s->stream));
             CK(cudaEventSynchronize(s->ev_b));
-            CK(cudaEventElapsedTime(&ts, s->ev_a, s->ev_b));
-            const int R_ = std::max(1, cands[k].rebuild_interval);
-            cost[k] = tb / R_ + ts / opts->trial_steps;
+            CK(cudaEventElapsedTime(&tp, s->ev_a, s->ev_b));
+            done_steps = probe;
+            const double probe_cost = tb / R_ + tp / probe;
+            if (probe < opts->trial_steps && best_k >= 0 && probe_cost > opts->probe_factor * cost[best_k]) {
+                cost[k] = probe_cost;
+                probed_out[k] = 1;
+                return LJSEL_OK;
+            }
+            if (probe < opts->trial_steps) {
+                CK(cudaEventRecord(s->ev_a, s->stream));
+                TRY(s->advance<R>(opts->trial_steps - probe, true));
+                CK(cudaEventRecord(s->ev_b, s->stream));
+                CK(cudaEventSynchronize(s->ev_b));
+                CK(cudaEventElapsedTime(&tr, s->ev_a, s->ev_b));
+                done_steps = opts->trial_steps;
+            }
+            cost[k] = tb / R_ + (tp + tr) / opts->trial_steps;
             return LJSEL_OK;
         });
+        if (st == LJSEL_ERR_UNSUPPORTED) { ent[k]->blacklisted = true; continue; }
         if (st != LJSEL_OK) return st;
-        steps_total += opts->trial_steps;
+        steps_total += done_steps;
         ent[k]->history.push_back({phase, cost[k]});
         if (ent[k]->history.size() > 8) ent[k]->history.erase(ent[k]->history.begin());
         ent[k]->last_trial_phase = phase;
         if (best_k < 0 || cost[k] < cost[best_k]) best_k = (int)k;
     }
     if (best_k < 0) { set_error("no candidate could be trialled"); return LJSEL_ERR_STATE; }
-    int nbl = 0, ntr = 0;
+    int nbl = 0, ntr = 0, npo = 0;
     double overhead = 0;
     for (size_t k = 0; k < cands.size(); ++k) {
         if (cost[k] < 0) continue;
         ++ntr;
-        overhead += (cost[k] - cost[best_k]) * opts->trial_steps;
+        npo += probed_out[k];
+        const int steps_k = probed_out[k] ? std::min(opts->probe_steps, opts->trial_steps) : opts->trial_steps;
+        overhead += (cost[k] - cost[best_k]) * steps_k;
         if (opts->blacklist_factor > 0 && cost[k] > opts->blacklist_factor * cost[best_k]) ent[k]->blacklisted = true;
     }
     for (auto *e : ent) nbl += e->blacklisted;
@@ -595,6 +688,8 @@ ljsel_status ljsel_autotune(ljsel_system h, const ljsel_tuner_opts *opts, ljsel_
     r.phase_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     r.overhead_ms = overhead;
     r.trial_steps_total = steps_total;
+    r.nprobed_out = npo;
+    r.expert_input = expert_x;
     s->last_report = r;
     if (chosen) *chosen = cands[best_k];
     if (report) *report = r;

@@ -148,10 +148,12 @@ std::vector<Buf *> System::all_bufs() {
 }
 
 void System::drop_graph() {
-    if (gexec) cudaGraphExecDestroy(gexec);
-    if (graph) cudaGraphDestroy(graph);
+    for (GraphEntry &e : gcache) {
+        if (e.exec) cudaGraphExecDestroy(e.exec);
+        if (e.graph) cudaGraphDestroy(e.graph);
+    }
+    gcache.clear();
     gexec = nullptr;
-    graph = nullptr;
 }
 
 size_t System::p4() const { return precision ? sizeof(D4) : sizeof(float4); }
@@ -279,7 +281,7 @@ ljsel_status System::apply_config() {
         LJ_TRY(grow(b_cp_count, (size_t)cp_stride * 4));
     }
     (void)grew;
-    drop_graph();
+    gexec = nullptr;  // the next advance looks the configuration up in the graph cache
     structure_dirty = true;
     return LJSEL_OK;
 }
@@ -467,24 +469,38 @@ template <typename R> ljsel_status System::ensure_structure() {
 }
 
 template <typename R> ljsel_status System::build_graph() {
-    drop_graph();
     if (!cap_stream) LJ_CUDA(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
     Dev<R> S;
     fill_dev(S);
+    GraphEntry e;
+    e.cfg = cfg;
+    e.key.assign(reinterpret_cast<const unsigned char *>(&S), reinterpret_cast<const unsigned char *>(&S) + sizeof(S));
+    cudaGraph_t graph = nullptr;
     LJ_CUDA(cudaGraphCreate(&graph, 0));
+    e.graph = graph;
+    auto fail = [&](cudaError_t err) {
+        cudaGraphDestroy(graph);
+        set_error(std::string("building the step graph failed: ") + cudaGetErrorString(err));
+        return LJSEL_ERR_CUDA;
+    };
+#define G_CK(call)                              \
+    do {                                        \
+        cudaError_t e_ = (call);                \
+        if (e_ != cudaSuccess) return fail(e_); \
+    } while (0)
     cudaGraphConditionalHandle h_loop, h_reb;
-    LJ_CUDA(cudaGraphConditionalHandleCreate(&h_loop, graph, 0, cudaGraphCondAssignDefault));
-    LJ_CUDA(cudaGraphConditionalHandleCreate(&h_reb, graph, 0, cudaGraphCondAssignDefault));
+    G_CK(cudaGraphConditionalHandleCreate(&h_loop, graph, 0, cudaGraphCondAssignDefault));
+    G_CK(cudaGraphConditionalHandleCreate(&h_reb, graph, 0, cudaGraphCondAssignDefault));
     // init node
-    LJ_CUDA(cudaStreamBeginCaptureToGraph(cap_stream, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    G_CK(cudaStreamBeginCaptureToGraph(cap_stream, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     launch_loop_init((Ctrl *)b_ctrl.ptr, h_reb, h_loop, cap_stream);
     cudaGraph_t tmp = nullptr;
-    LJ_CUDA(cudaStreamEndCapture(cap_stream, &tmp));
+    G_CK(cudaStreamEndCapture(cap_stream, &tmp));
     size_t nn = 0;
-    LJ_CUDA(cudaGraphGetNodes(graph, nullptr, &nn));
+    G_CK(cudaGraphGetNodes(graph, nullptr, &nn));
     std::vector<cudaGraphNode_t> nodes(nn);
-    LJ_CUDA(cudaGraphGetNodes(graph, nodes.data(), &nn));
-    if (nn != 1) { set_error("unexpected node count while building the step graph"); return LJSEL_ERR_CUDA; }
+    G_CK(cudaGraphGetNodes(graph, nodes.data(), &nn));
+    if (nn != 1) { cudaGraphDestroy(graph); set_error("unexpected node count while building the step graph"); return LJSEL_ERR_CUDA; }
     // WHILE node
     cudaGraphNodeParams wp = {};
     wp.type = cudaGraphNodeTypeConditional;
@@ -492,7 +508,7 @@ template <typename R> ljsel_status System::build_graph() {
     wp.conditional.type = cudaGraphCondTypeWhile;
     wp.conditional.size = 1;
     cudaGraphNode_t wnode;
-    LJ_CUDA(cudaGraphAddNode(&wnode, graph, nodes.data(), nullptr, 1, &wp));
+    G_CK(cudaGraphAddNode(&wnode, graph, nodes.data(), nullptr, 1, &wp));
     cudaGraph_t body = wp.conditional.phGraph_out[0];
     // IF(rebuild) inside the loop body
     cudaGraphNodeParams ip = {};
@@ -501,28 +517,53 @@ template <typename R> ljsel_status System::build_graph() {
     ip.conditional.type = cudaGraphCondTypeIf;
     ip.conditional.size = 1;
     cudaGraphNode_t inode;
-    LJ_CUDA(cudaGraphAddNode(&inode, body, nullptr, nullptr, 0, &ip));
+    G_CK(cudaGraphAddNode(&inode, body, nullptr, nullptr, 0, &ip));
     cudaGraph_t rbody = ip.conditional.phGraph_out[0];
-    LJ_CUDA(cudaStreamBeginCaptureToGraph(cap_stream, rbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    G_CK(cudaStreamBeginCaptureToGraph(cap_stream, rbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     enqueue_rebuild(S, cap_stream);
-    LJ_CUDA(cudaStreamEndCapture(cap_stream, &tmp));
+    G_CK(cudaStreamEndCapture(cap_stream, &tmp));
     // step kernels + control, after the IF node
-    LJ_CUDA(cudaStreamBeginCaptureToGraph(cap_stream, body, &inode, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+    G_CK(cudaStreamBeginCaptureToGraph(cap_stream, body, &inode, nullptr, 1, cudaStreamCaptureModeThreadLocal));
     enqueue_step(S, false, cap_stream);
     launch_control((Ctrl *)b_ctrl.ptr, h_reb, h_loop, 1, cap_stream);
-    LJ_CUDA(cudaStreamEndCapture(cap_stream, &tmp));
-    LJ_CUDA(cudaGraphInstantiate(&gexec, graph, 0));
+    G_CK(cudaStreamEndCapture(cap_stream, &tmp));
+    G_CK(cudaGraphInstantiate(&e.exec, graph, 0));
+#undef G_CK
+    if (gcache.size() >= 48) {  // drop the oldest entry
+        cudaGraphExecDestroy(gcache.front().exec);
+        cudaGraphDestroy(gcache.front().graph);
+        gcache.erase(gcache.begin());
+    }
+    gcache.push_back(e);
+    gexec = e.exec;
     return LJSEL_OK;
 }
 
-template <typename R> ljsel_status System::advance(long long nsteps) {
+// Reuse the cached graph of this configuration when the kernel-parameter
+// block (every pointer, size and capacity baked into the graph) is unchanged.
+template <typename R> ljsel_status System::ensure_graph() {
+    if (gexec) return LJSEL_OK;
+    Dev<R> S;
+    fill_dev(S);
+    const unsigned char *kb = reinterpret_cast<const unsigned char *>(&S);
+    for (GraphEntry &e : gcache) {
+        if (e.key.size() == sizeof(S) && memcmp(e.key.data(), kb, sizeof(S)) == 0 &&
+            memcmp(&e.cfg, &cfg, sizeof(cfg)) == 0) {
+            gexec = e.exec;
+            return LJSEL_OK;
+        }
+    }
+    return build_graph<R>();
+}
+
+template <typename R> ljsel_status System::advance(long long nsteps, bool eager) {
     if (nsteps <= 0) return LJSEL_OK;
     LJ_TRY(ensure_structure<R>());
     long long left = nsteps;
     for (int round = 0; round < 16 && left > 0; ++round) {
         LJ_TRY(cmd(CMD_BEGIN, left));
-        if (params.use_graphs) {
-            if (!gexec) LJ_TRY(build_graph<R>());
+        if (params.use_graphs && !eager) {
+            LJ_TRY(ensure_graph<R>());
             LJ_CUDA(cudaGraphLaunch(gexec, stream));
         } else {
             Dev<R> S;
@@ -640,7 +681,8 @@ template <typename R> ljsel_status System::profile(long long nsteps, ljsel_profi
     template void System::enqueue_step<R>(const Dev<R> &, bool, cudaStream_t); \
     template ljsel_status System::ensure_structure<R>();               \
     template ljsel_status System::build_graph<R>();                    \
-    template ljsel_status System::advance<R>(long long);               \
+    template ljsel_status System::ensure_graph<R>();                   \
+    template ljsel_status System::advance<R>(long long, bool);         \
     template ljsel_status System::compute_forces<R>(bool);             \
     template ljsel_status System::sync_velocities<R>();                \
     template ljsel_status System::profile<R>(long long, ljsel_profile *);

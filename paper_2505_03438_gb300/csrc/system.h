@@ -28,6 +28,15 @@ struct TunerEntry {
     bool blacklisted = false;
 };
 
+// One instantiated step graph, valid for exactly the configuration and
+// device layout (the bytes of the kernel-parameter block) it was built for.
+struct GraphEntry {
+    ljsel_config cfg;
+    std::vector<unsigned char> key;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
 struct System {
     ljsel_params params{};
     int n = 0;
@@ -59,8 +68,9 @@ struct System {
     Buf b_ctrl, b_io;
     Ctrl *h_ctrl = nullptr;  // pinned mirror
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
-    // graph of the stepping loop for the current configuration
-    cudaGraph_t graph = nullptr;
+    // step graphs, one per (configuration, device layout); gexec is the
+    // current configuration's
+    std::vector<GraphEntry> gcache;
     cudaGraphExec_t gexec = nullptr;
     // tuner state
     std::vector<TunerEntry> tuner;
@@ -83,7 +93,8 @@ struct System {
     template <typename R> void enqueue_step(const Dev<R> &S, bool ev, cudaStream_t st);
     template <typename R> ljsel_status ensure_structure();
     template <typename R> ljsel_status build_graph();
-    template <typename R> ljsel_status advance(long long nsteps);
+    template <typename R> ljsel_status ensure_graph();
+    template <typename R> ljsel_status advance(long long nsteps, bool eager = false);
     template <typename R> ljsel_status compute_forces(bool ev);
     template <typename R> ljsel_status sync_velocities();
     template <typename R> ljsel_status profile(long long nsteps, ljsel_profile *out);

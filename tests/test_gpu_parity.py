@@ -240,8 +240,20 @@ def test_autotune_full_and_predictive(lj):
         _, rep = s2.autotune(strategy=1, trial_steps=10, blacklist_factor=10.0)
     assert rep["ntrialled"] < len(cands)
     check_against_oracle(s2, sc)
-    s.close()
-    s2.close()
+    # probe filter: slow configurations stop after their probe steps
+    s3 = lj.System(sc)
+    _, rep = s3.autotune(strategy=0, trial_steps=10, probe_steps=2, probe_factor=1.5)
+    assert rep["nprobed_out"] > 0 and rep["trial_steps_total"] < 10 * len(cands)
+    assert s3.counters()["steps"] == rep["trial_steps_total"]
+    check_against_oracle(s3, sc)
+    # expert strategy: the dense liquid (about 16 particles per bin) trials a subset
+    s4 = lj.System(sc)
+    chosen4, rep = s4.autotune(strategy="expert", trial_steps=5)
+    assert rep["expert_input"] > 8 and 0 < rep["ntrialled"] < len(cands)
+    assert chosen4.method == lj.METHOD_VL
+    check_against_oracle(s4, sc)
+    for x in (s, s2, s3, s4):
+        x.close()
 
 
 def test_device_pointer_inputs(lj):
