@@ -55,6 +55,7 @@ class Params(ctypes.Structure):
 
 _D = ctypes.POINTER(ctypes.c_double)
 _I32 = ctypes.POINTER(ctypes.c_int32)
+_I64 = ctypes.POINTER(ctypes.c_int64)
 
 
 def _bind(lib):
@@ -72,6 +73,17 @@ def _bind(lib):
     lib.orc_verlet_run.restype = ctypes.c_int32
     lib.orc_bin_stats.argtypes = [ctypes.c_int64, _D, _D, ctypes.c_double, _D]
     lib.orc_bin_stats.restype = None
+    lib.orc_forces_list.argtypes = [ctypes.c_int64, _D, _I32, ctypes.POINTER(Params), _I32, ctypes.c_int64, _D]
+    lib.orc_forces_list.restype = None
+    lib.orc_force_vjp.argtypes = [ctypes.c_int64, _D, _I32, ctypes.POINTER(Params), _I32, ctypes.c_int64, _D,
+                                  _D, _D, _D]
+    lib.orc_force_vjp.restype = None
+    lib.orc_rollout.argtypes = [ctypes.c_int64, _D, _D, _I32, _D, ctypes.POINTER(Params), ctypes.c_double,
+                                ctypes.c_int64, _D, _D, _I32, _I64, _I32, ctypes.c_int64, _I64]
+    lib.orc_rollout.restype = ctypes.c_int64
+    lib.orc_rollout_vjp.argtypes = [ctypes.c_int64, _D, _D, _I32, _D, ctypes.POINTER(Params), ctypes.c_double,
+                                    ctypes.c_int64, _D, _D, _D, _D, _D, _D]
+    lib.orc_rollout_vjp.restype = None
     return lib
 
 
@@ -223,3 +235,120 @@ def sorted_pairs(p):
     hi = np.maximum(p[:, 0], p[:, 1])
     order = np.lexsort((hi, lo))
     return np.stack([lo[order], hi[order]], 1)
+
+
+# ---------------------------------------------------------------------------
+# Gradients (the differentiable binary-mixture workload; the pair mask is
+# frozen at the evaluation point, see ljoracle.c)
+
+
+def _pairs_arr(pairs):
+    return np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+
+
+def forces_list(x, types, params: Params, pairs, lib=None):
+    """Forces over a fixed list of unordered pairs (frozen mask), minimum image."""
+    lib = lib or load()
+    x, types, n = _prep(x, types)
+    pr = _pairs_arr(pairs)
+    F = np.zeros((n, 3))
+    lib.orc_forces_list(n, _dp(x), _ip(types), ctypes.byref(params), _ip(pr), pr.shape[0], _dp(F))
+    return F
+
+
+def force_vjp(x, types, params: Params, pairs, cot, lib=None):
+    """(dF/dx)^T cot and d(cot . F)/d(eps, sigma) over a frozen pair list.
+
+    Returns (gx [n, 3], geps [nt, nt], gsig [nt, nt]); entries (a, b) and
+    (b, a) of geps/gsig both hold the derivative for the shared parameter.
+    """
+    lib = lib or load()
+    x, types, n = _prep(x, types)
+    pr = _pairs_arr(pairs)
+    c = np.ascontiguousarray(cot, dtype=np.float64).reshape(n, 3)
+    nt = params.ntypes
+    gx = np.zeros((n, 3))
+    ge = np.zeros(nt * nt)
+    gs = np.zeros(nt * nt)
+    lib.orc_force_vjp(n, _dp(x), _ip(types), ctypes.byref(params), _ip(pr), pr.shape[0], _dp(c),
+                      _dp(gx), _dp(ge), _dp(gs))
+    return gx, ge.reshape(nt, nt), gs.reshape(nt, nt)
+
+
+def rollout(x0, v0, types, mass, params: Params, dt, nsteps, frozen=None, lib=None):
+    """Unwrapped velocity-form Stormer-Verlet (Sec. 2.1) for gradient checks.
+
+    Returns (xs [nsteps+1, n, 3], vs [...], masks, offsets): with ``frozen``
+    = (masks, offsets) of an earlier run the pair mask of every time level is
+    taken from it instead of being recomputed.
+    """
+    lib = lib or load()
+    x0, types, n = _prep(x0, types)
+    v0 = np.ascontiguousarray(v0, dtype=np.float64).reshape(n, 3)
+    mass = np.ascontiguousarray(np.atleast_1d(np.asarray(mass, np.float64)))
+    xs = np.zeros((nsteps + 1, n, 3))
+    vs = np.zeros((nsteps + 1, n, 3))
+    if frozen is not None:
+        masks, off = _pairs_arr(frozen[0]), np.ascontiguousarray(frozen[1], dtype=np.int64)
+        lib.orc_rollout(n, _dp(x0), _dp(v0), _ip(types), _dp(mass), ctypes.byref(params), float(dt), int(nsteps),
+                        _dp(xs), _dp(vs), _ip(masks), off.ctypes.data_as(_I64), None, 0, None)
+        return xs, vs, masks, off
+    off = np.zeros(nsteps + 2, np.int64)
+    cap = 0
+    masks = np.zeros((1, 2), np.int32)
+    for _ in range(2):
+        total = lib.orc_rollout(n, _dp(x0), _dp(v0), _ip(types), _dp(mass), ctypes.byref(params), float(dt),
+                                int(nsteps), _dp(xs), _dp(vs), None, None, _ip(masks), cap,
+                                off.ctypes.data_as(_I64))
+        if total <= cap:
+            return xs, vs, masks[:total], off
+        cap = int(total)
+        masks = np.zeros((cap, 2), np.int32)
+    raise RuntimeError("rollout masks changed between two identical runs")
+
+
+def rollout_vjp(x0, v0, types, mass, params: Params, dt, nsteps, xbar, vbar, lib=None):
+    """Cotangents of (x_0, v_0, eps, sigma) from those of (x_N, v_N) through N steps."""
+    lib = lib or load()
+    x0, types, n = _prep(x0, types)
+    v0 = np.ascontiguousarray(v0, dtype=np.float64).reshape(n, 3)
+    mass = np.ascontiguousarray(np.atleast_1d(np.asarray(mass, np.float64)))
+    xb = np.ascontiguousarray(xbar, dtype=np.float64).reshape(n, 3)
+    vb = np.ascontiguousarray(vbar, dtype=np.float64).reshape(n, 3)
+    nt = params.ntypes
+    gx, gv = np.zeros((n, 3)), np.zeros((n, 3))
+    ge, gs = np.zeros(nt * nt), np.zeros(nt * nt)
+    lib.orc_rollout_vjp(n, _dp(x0), _dp(v0), _ip(types), _dp(mass), ctypes.byref(params), float(dt), int(nsteps),
+                        _dp(xb), _dp(vb), _dp(gx), _dp(gv), _dp(ge), _dp(gs))
+    return gx, gv, ge.reshape(nt, nt), gs.reshape(nt, nt)
+
+
+def force_loss(F, Fstar):
+    """Mean squared force difference L = sum |F - F*|^2 / (3N)."""
+    d = np.asarray(F) - np.asarray(Fstar)
+    return float((d * d).sum() / d.size)
+
+
+def force_loss_grad(x, types, params: Params, Fstar, pairs=None, lib=None):
+    """Loss and its gradient w.r.t. positions and (eps, sigma) at one configuration.
+
+    The pair mask is that of x under ``params`` unless ``pairs`` is given.
+    Returns (L, gx, geps, gsig).
+    """
+    lib = lib or load()
+    if pairs is None:
+        pairs = forces_cells(x, types, params, pairs=True, lib=lib)["pairs"]
+    F = forces_list(x, types, params, pairs, lib=lib)
+    cot = 2.0 * (F - Fstar) / F.size
+    gx, ge, gs = force_vjp(x, types, params, pairs, cot, lib=lib)
+    return force_loss(F, Fstar), gx, ge, gs
+
+
+def rollout_loss_grad(x0, v0, types, mass, params: Params, dt, nsteps, Fstar_end, lib=None):
+    """L = mean |F(x_N) - F*|^2 after N steps, and its gradient w.r.t. x_0, v_0, eps, sigma."""
+    lib = lib or load()
+    xs, _, masks, off = rollout(x0, v0, types, mass, params, dt, nsteps, lib=lib)
+    pe = masks[off[nsteps]:off[nsteps + 1]]
+    L, gxN, ge1, gs1 = force_loss_grad(xs[nsteps], types, params, Fstar_end, pairs=pe, lib=lib)
+    gx0, gv0, ge2, gs2 = rollout_vjp(x0, v0, types, mass, params, dt, nsteps, gxN, np.zeros_like(gxN), lib=lib)
+    return L, gx0, gv0, ge1 + ge2, gs1 + gs2

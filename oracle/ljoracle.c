@@ -381,3 +381,218 @@ void orc_bin_stats(int64_t n, const double *x, const double *box, double bin_min
     out[5] = (double)nempty;
     free(cnt);
 }
+
+/* ---------------------------------------------------------------------- */
+/* Gradients of the force field (the differentiable binary mixture of the  *
+ * workload list; the paper itself has no gradient).  Readings, listed in  *
+ * the design notes:                                                       *
+ *   - the pair set (the mask r^2 < r_c,ab^2) is frozen at the evaluation  *
+ *     point, so derivatives are the almost-everywhere derivatives of a    *
+ *     fixed sum, and finite differences use the same frozen set;          *
+ *   - eps_ab and sigma_ab are one parameter per unordered type pair; the  *
+ *     gradient entry (a,b) and (b,a) both hold the derivative with        *
+ *     respect to that shared parameter;                                   *
+ *   - the energy shift does not enter the force, so it has no gradient.   *
+ * With s = r^2 the force on i from j is g(s) r_ij, r_ij = x_i - (x_j+kL): *
+ *   g       = 24 eps (2 sig^12 / s^7 - sig^6 / s^4)                       *
+ *   dg/ds   = 24 eps (-14 sig^12 / s^8 + 4 sig^6 / s^5)                   *
+ *   dg/deps = 24 (2 sig^12 / s^7 - sig^6 / s^4)                           *
+ *   dg/dsig = 24 eps (24 sig^11 / s^7 - 6 sig^5 / s^4)                    *
+ * and d(g r)/dr = g I + 2 dg/ds r r^T.                                    */
+static void lj_force_derivs(double s, double eps, double sig, double *g, double *dg_ds,
+                            double *dg_deps, double *dg_dsig)
+{
+    double sig2 = sig * sig;
+    double sig5 = sig2 * sig2 * sig;
+    double sig6 = sig5 * sig;
+    double sig11 = sig6 * sig5;
+    double sig12 = sig6 * sig6;
+    double s2 = s * s;
+    double s4 = s2 * s2;
+    double s5 = s4 * s;
+    double s7 = s4 * s2 * s;
+    double s8 = s4 * s4;
+    *dg_deps = 24.0 * (2.0 * sig12 / s7 - sig6 / s4);
+    *g = eps * *dg_deps;
+    *dg_ds = 24.0 * eps * (-14.0 * sig12 / s8 + 4.0 * sig6 / s5);
+    *dg_dsig = 24.0 * eps * (24.0 * sig11 / s7 - 6.0 * sig5 / s4);
+}
+
+static void pair_dx(const double *x, int64_t i, int64_t j, const orc_params *p, double r[3])
+{
+    for (int d = 0; d < 3; ++d)
+        r[d] = image_dx(x[3*i+d], x[3*j+d], p->box[d], min_image_k(x[3*i+d], x[3*j+d], p->box[d]));
+}
+
+/* Forces over a given list of unordered pairs (the frozen mask), minimum  *
+ * image, no cutoff test.                                                  */
+void orc_forces_list(int64_t n, const double *x, const int32_t *type, const orc_params *p,
+                     const int32_t *pairs, int64_t npairs, double *F)
+{
+    int nt = p->ntypes;
+    memset(F, 0, sizeof(double) * 3 * (size_t)n);
+    for (int64_t k = 0; k < npairs; ++k) {
+        int64_t i = pairs[2*k], j = pairs[2*k+1];
+        int t = type[i] * nt + type[j];
+        double r[3];
+        pair_dx(x, i, j, p, r);
+        double f, u;
+        lj_terms(r2_of(r[0], r[1], r[2]), p->eps[t], p->sigma[t], &f, &u);
+        for (int d = 0; d < 3; ++d) {
+            F[3*i+d] += f * r[d];
+            F[3*j+d] -= f * r[d];
+        }
+    }
+}
+
+/* Vector-Jacobian product of the forces over a frozen pair list.  Given   *
+ * the cotangent c = dL/dF (n x 3): gx = (dF/dx)^T c (n x 3; a Hessian-    *
+ * vector product, since dF/dx = -Hessian of U), and geps/gsig (ntypes^2)  *
+ * = d(c . F)/d eps_ab, d(c . F)/d sig_ab.                                 */
+void orc_force_vjp(int64_t n, const double *x, const int32_t *type, const orc_params *p,
+                   const int32_t *pairs, int64_t npairs, const double *c,
+                   double *gx, double *geps, double *gsig)
+{
+    int nt = p->ntypes;
+    memset(gx, 0, sizeof(double) * 3 * (size_t)n);
+    memset(geps, 0, sizeof(double) * (size_t)(nt * nt));
+    memset(gsig, 0, sizeof(double) * (size_t)(nt * nt));
+    for (int64_t k = 0; k < npairs; ++k) {
+        int64_t i = pairs[2*k], j = pairs[2*k+1];
+        int a = type[i], b = type[j];
+        int t = a * nt + b;
+        double r[3], u[3];
+        pair_dx(x, i, j, p, r);
+        double s = r2_of(r[0], r[1], r[2]);
+        double g, dgds, dgde, dgdsig;
+        lj_force_derivs(s, p->eps[t], p->sigma[t], &g, &dgds, &dgde, &dgdsig);
+        /* the pair adds g r to F_i and -g r to F_j: c . F gets (c_i - c_j) . g r */
+        for (int d = 0; d < 3; ++d) u[d] = c[3*i+d] - c[3*j+d];
+        double ur = u[0] * r[0] + u[1] * r[1] + u[2] * r[2];
+        for (int d = 0; d < 3; ++d) {
+            double w = g * u[d] + 2.0 * dgds * ur * r[d];
+            gx[3*i+d] += w;
+            gx[3*j+d] -= w;
+        }
+        geps[t] += ur * dgde;
+        gsig[t] += ur * dgdsig;
+        if (a != b) {
+            geps[b * nt + a] += ur * dgde;
+            gsig[b * nt + a] += ur * dgdsig;
+        }
+    }
+}
+
+/* In-range pair set at x (linked cells), into a fresh buffer, sorted so  *
+ * that every sum over it runs in one fixed order.                         */
+static int cmp_pair(const void *a, const void *b)
+{
+    const int32_t *x = (const int32_t *)a, *y = (const int32_t *)b;
+    if (x[0] != y[0]) return (x[0] > y[0]) - (x[0] < y[0]);
+    return (x[1] > y[1]) - (x[1] < y[1]);
+}
+
+static int32_t *pairs_at(int64_t n, const double *x, const int32_t *type, const orc_params *p,
+                         double *F, int64_t *np_out)
+{
+    double rcmax = 0.0;
+    for (int t = 0; t < p->ntypes * p->ntypes; ++t) if (p->rcut[t] > rcmax) rcmax = p->rcut[t];
+    int64_t np = orc_forces_cells(n, x, type, p, rcmax, 0, F, NULL, NULL, NULL, 0);
+    int32_t *pr = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)(np > 0 ? np : 1));
+    orc_forces_cells(n, x, type, p, rcmax, 0, F, NULL, NULL, pr, np);
+    qsort(pr, (size_t)np, 2 * sizeof(int32_t), cmp_pair);
+    *np_out = np;
+    return pr;
+}
+
+/* Velocity-form Stormer-Verlet (Sec. 2.1) for a differentiated rollout:   *
+ * positions are not wrapped (a shift by L changes no force), and the pair *
+ * mask of time level t (t = 0 .. nsteps) is either computed (linked       *
+ * cells; appended to masks_out with offsets off_out[t] .. off_out[t+1]    *
+ * while it fits in cap pairs) or taken frozen from frozen[off[t] ..       *
+ * off[t+1]).  xs, vs (optional) receive x_t, v_t for t = 0 .. nsteps.     *
+ * Returns the number of mask pairs over all levels.                       */
+int64_t orc_rollout(int64_t n, const double *x0, const double *v0, const int32_t *type,
+                    const double *mass, const orc_params *p, double dt, int64_t nsteps,
+                    double *xs, double *vs, const int32_t *frozen, const int64_t *off,
+                    int32_t *masks_out, int64_t cap, int64_t *off_out)
+{
+    size_t n3 = 3 * (size_t)n;
+    double *x = (double *)malloc(sizeof(double) * (n3 ? n3 : 1));
+    double *v = (double *)malloc(sizeof(double) * (n3 ? n3 : 1));
+    double *F = (double *)malloc(sizeof(double) * (n3 ? n3 : 1));
+    memcpy(x, x0, sizeof(double) * n3);
+    memcpy(v, v0, sizeof(double) * n3);
+    int64_t used = 0;
+    for (int64_t t = 0; t <= nsteps; ++t) {
+        /* forces at x_t */
+        if (frozen) {
+            orc_forces_list(n, x, type, p, frozen + 2 * off[t], off[t+1] - off[t], F);
+        } else {
+            int64_t np;
+            int32_t *pr = pairs_at(n, x, type, p, F, &np);
+            if (off_out) off_out[t] = used;
+            if (masks_out && used + np <= cap) memcpy(masks_out + 2 * used, pr, sizeof(int32_t) * 2 * (size_t)np);
+            used += np;
+            if (off_out) off_out[t + 1] = used;
+            free(pr);
+        }
+        if (t > 0)  /* second half kick of step t-1 */
+            for (int64_t i = 0; i < n; ++i)
+                for (int d = 0; d < 3; ++d) v[3*i+d] += 0.5 * dt / mass[type[i]] * F[3*i+d];
+        if (xs) memcpy(xs + (size_t)t * n3, x, sizeof(double) * n3);
+        if (vs) memcpy(vs + (size_t)t * n3, v, sizeof(double) * n3);
+        if (t == nsteps) break;
+        /* first half kick and drift of step t */
+        for (int64_t i = 0; i < n; ++i)
+            for (int d = 0; d < 3; ++d) {
+                v[3*i+d] += 0.5 * dt / mass[type[i]] * F[3*i+d];
+                x[3*i+d] += dt * v[3*i+d];
+            }
+    }
+    free(x); free(v); free(F);
+    return used;
+}
+
+/* Reverse-mode derivative of orc_rollout (mask computed per level): given *
+ * the cotangents xbar, vbar of x_N, v_N, returns those of x_0, v_0 and of  *
+ * eps/sigma.  Each step v_h = v_t + c F(x_t), x_{t+1} = x_t + dt v_h,      *
+ * v_{t+1} = v_h + c F(x_{t+1}) (c = dt / 2m) is reversed in the opposite   *
+ * order, one force VJP per kick.                                          */
+void orc_rollout_vjp(int64_t n, const double *x0, const double *v0, const int32_t *type,
+                     const double *mass, const orc_params *p, double dt, int64_t nsteps,
+                     const double *xbar, const double *vbar, double *gx0, double *gv0,
+                     double *geps, double *gsig)
+{
+    int nt = p->ntypes;
+    size_t n3 = 3 * (size_t)n;
+    double *xs = (double *)malloc(sizeof(double) * (n3 ? n3 : 1) * (size_t)(nsteps + 1));
+    double *F = (double *)malloc(sizeof(double) * (n3 ? n3 : 1));
+    double *cot = (double *)malloc(sizeof(double) * (n3 ? n3 : 1));
+    double *g = (double *)malloc(sizeof(double) * (n3 ? n3 : 1));
+    double ge[ORC_MAX_TYPES * ORC_MAX_TYPES], gs[ORC_MAX_TYPES * ORC_MAX_TYPES];
+    orc_rollout(n, x0, v0, type, mass, p, dt, nsteps, xs, NULL, NULL, NULL, NULL, 0, NULL);
+    memcpy(gx0, xbar, sizeof(double) * n3);
+    memcpy(gv0, vbar, sizeof(double) * n3);
+    memset(geps, 0, sizeof(double) * (size_t)(nt * nt));
+    memset(gsig, 0, sizeof(double) * (size_t)(nt * nt));
+    for (int64_t t = nsteps - 1; t >= 0; --t) {
+        for (int level = 1; level >= 0; --level) {
+            /* level 1: the kick v_{t+1} = v_h + c F(x_{t+1}); level 0: the kick
+             * v_h = v_t + c F(x_t).  Between them, the drift passes dt * xbar
+             * on to the velocity cotangent. */
+            const double *xl = xs + (size_t)(t + level) * n3;
+            for (int64_t i = 0; i < n; ++i)
+                for (int d = 0; d < 3; ++d) cot[3*i+d] = 0.5 * dt / mass[type[i]] * gv0[3*i+d];
+            int64_t np;
+            int32_t *pr = pairs_at(n, xl, type, p, F, &np);
+            orc_force_vjp(n, xl, type, p, pr, np, cot, g, ge, gs);
+            free(pr);
+            for (size_t k = 0; k < n3; ++k) gx0[k] += g[k];
+            for (int k = 0; k < nt * nt; ++k) { geps[k] += ge[k]; gsig[k] += gs[k]; }
+            if (level == 1)
+                for (size_t k = 0; k < n3; ++k) gv0[k] += dt * gx0[k];
+        }
+    }
+    free(xs); free(F); free(cot); free(g);
+}

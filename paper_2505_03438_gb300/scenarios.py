@@ -158,3 +158,29 @@ def random_gas(n: int, box_len: float, seed: int, min_dist=0.0, rc=2.5, skin=0.3
               temperature=temperature)
     sc.update(_single_type(np.full(3, box_len), rc))
     return sc
+
+
+def perturbed_pair_params(eps, sigma, seed=5, frac=0.05):
+    """Target parameters of the force-matching workload: every independent
+    eps_ab, sigma_ab (a <= b) times (1 + u), u ~ U(-frac, frac) from a seeded
+    PCG64 stream, kept symmetric.  The target cutoffs are 2.5 sigma*_ab."""
+    rng = np.random.default_rng(seed + 1000)
+    eps = np.array(eps, np.float64, copy=True)
+    sigma = np.array(sigma, np.float64, copy=True)
+    nt = eps.shape[0]
+    for a in range(nt):
+        for b in range(a, nt):
+            ue, us = rng.uniform(-frac, frac, 2)
+            eps[a, b] = eps[b, a] = eps[a, b] * (1.0 + ue)
+            sigma[a, b] = sigma[b, a] = sigma[a, b] * (1.0 + us)
+    return eps, sigma, 2.5 * sigma
+
+
+def jittered_mixture(nside=7, seed=5, jitter=0.1):
+    """The binary mixture on a small lattice with uniform +-jitter per
+    coordinate, so that no force vanishes by symmetry (gradient checks)."""
+    sc = binary_mixture(seed=seed, nside=nside)
+    rng = np.random.default_rng(seed + 2000)
+    sc["x"] = sc["x"] + rng.uniform(-jitter, jitter, sc["x"].shape)
+    sc["name"] = "binary_%d_jittered" % len(sc["x"])
+    return sc

@@ -247,6 +247,195 @@ def pin_bin_stats(lib):
     assert st["nbins"] == 2 and st["median"] == 2.0
 
 
+# ---------------------------------------------------------------------------
+# Gradients (frozen pair mask)
+
+
+def _mix_params(sc, eps=None, sigma=None, rcut=None, box=None):
+    return oracle.make_params(sc["box"] if box is None else box, sc["eps"] if eps is None else eps,
+                              sc["sigma"] if sigma is None else sigma, sc["rcut"] if rcut is None else rcut, True)
+
+
+def pin_vjp_two_body(lib):
+    """Closed-form Hessian and parameter derivatives of one isolated pair."""
+    rng = np.random.default_rng(11)
+    for eps, sig, r in [(1.0, 1.0, 1.05), (1.5, 0.8, 1.3), (0.5, 0.88, 2.0)]:
+        d = rng.normal(size=3)
+        rhat = d / np.linalg.norm(d)
+        x = np.array([[10.0, 10.0, 10.0], [10.0, 10.0, 10.0]])
+        x[1] -= r * rhat  # x_0 - x_1 = r rhat
+        rhat = (x[0] - x[1]) / np.linalg.norm(x[0] - x[1])
+        r = np.linalg.norm(x[0] - x[1])
+        e = np.array([[0.7, eps], [eps, 1.9]])
+        s = np.array([[1.1, sig], [sig, 0.9]])
+        p = oracle.make_params(20.0, e, s, 2.5 * s, True)
+        types = np.array([0, 1], np.int32)
+        # phi(r) = 4 eps (sig^12 r^-12 - sig^6 r^-6) and its r-derivatives
+        d1 = 4 * eps * (-12 * sig**12 * r**-13 + 6 * sig**6 * r**-7)
+        d2 = 4 * eps * (156 * sig**12 * r**-14 - 42 * sig**6 * r**-8)
+        d1_dsig = 4 * eps * (-144 * sig**11 * r**-13 + 36 * sig**5 * r**-7)
+        P = np.outer(rhat, rhat)
+        H = d2 * P + (d1 / r) * (np.eye(3) - P)
+        F0 = -d1 * rhat
+        for who in (0, 1):
+            c = np.zeros((2, 3))
+            c[who] = rng.normal(size=3)
+            gx, ge, gs = oracle.force_vjp(x, types, p, [[0, 1]], c, lib=lib)
+            # dF_a/dx_b = -d^2U/dx_a dx_b: -H on the diagonal blocks, +H off it
+            want = np.zeros((2, 3))
+            want[who] = -H @ c[who]
+            want[1 - who] = H @ c[who]
+            assert np.abs(gx - want).max() < 1e-11 * np.abs(want).max(), (who, gx, want)
+            Fw = F0 if who == 0 else -F0
+            ge_want = c[who] @ Fw / eps
+            gs_want = c[who] @ (-d1_dsig * rhat) * (1 if who == 0 else -1)
+            for a, b in ((0, 1), (1, 0)):
+                assert abs(ge[a, b] - ge_want) < 1e-12 * abs(ge_want) + 1e-300, (ge, ge_want)
+                assert abs(gs[a, b] - gs_want) < 1e-12 * abs(gs_want) + 1e-300, (gs, gs_want)
+            assert ge[0, 0] == 0 and ge[1, 1] == 0 and gs[0, 0] == 0 and gs[1, 1] == 0
+
+
+def pin_vjp_invariants(lib):
+    """Translation invariance, Hessian symmetry, eps-linearity, the scaling
+    law F(lx; l sigma) = F(x; sigma) / l, and the frozen-list forces equal to
+    brute force."""
+    sc = scenarios.jittered_mixture(nside=7)
+    x, types = sc["x"], sc["types"]
+    p = _mix_params(sc)
+    ref = oracle.forces_brute(x, types, p, pairs=True, lib=lib)
+    pairs = ref["pairs"]
+    F = oracle.forces_list(x, types, p, pairs, lib=lib)
+    assert np.abs(F - ref["F"]).max() < 1e-12 * np.abs(ref["F"]).max()
+    rng = np.random.default_rng(12)
+    c = rng.normal(size=x.shape)
+    gx, ge, gs = oracle.force_vjp(x, types, p, pairs, c, lib=lib)
+    scale = np.abs(gx).sum()
+    assert np.abs(gx.sum(0)).max() < 1e-12 * scale, gx.sum(0)
+    iu = np.triu_indices(2)
+    cF = float((c * F).sum())
+    assert abs((sc["eps"][iu] * ge[iu]).sum() - cF) < 1e-11 * abs(cF)
+    u = rng.normal(size=x.shape)
+    gu = oracle.force_vjp(x, types, p, pairs, u, lib=lib)[0]
+    a, b = float((u * gx).sum()), float((c * gu).sum())
+    assert abs(a - b) < 1e-11 * (abs(a) + abs(b)), (a, b)
+    # Euler identity for the scaling law needs displacements without images:
+    # the same cluster placed inside a large box
+    xb = x + 10.0
+    pb = _mix_params(sc, box=40.0)
+    Fb = oracle.forces_list(xb, types, pb, pairs, lib=lib)
+    gxb, geb, gsb = oracle.force_vjp(xb, types, pb, pairs, c, lib=lib)
+    lhs = (sc["sigma"][iu] * gsb[iu]).sum() + float((xb * gxb).sum())
+    rhs = -float((c * Fb).sum())
+    assert abs(lhs - rhs) < 1e-10 * abs(rhs), (lhs, rhs)
+
+
+def _theta_params(sc, eps, sigma, k, h):
+    """Parameters with the k-th independent value (eps_00, sig_00, eps_01, ...) scaled by (1 + h)."""
+    eps, sigma = eps.copy(), sigma.copy()
+    iu = list(zip(*np.triu_indices(eps.shape[0])))
+    a, b = iu[k // 2]
+    arr = eps if k % 2 == 0 else sigma
+    arr[a, b] = arr[b, a] = arr[a, b] * (1.0 + h)
+    return _mix_params(sc, eps=eps, sigma=sigma)  # cutoffs unchanged: the mask stays frozen
+
+
+def _theta_grad(ge, gs):
+    return np.array([g[a, b] for a, b in zip(*np.triu_indices(ge.shape[0])) for g in (ge, gs)])
+
+
+def _theta_vals(sc):
+    return _theta_grad(sc["eps"], sc["sigma"])
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+def pin_vjp_finite_difference(lib, h=1e-6):
+    """Force-matching loss: analytic gradient vs central differences with the
+    mask frozen, relative step h for eps/sigma, absolute h for 64 coordinates."""
+    sc = scenarios.jittered_mixture(nside=7)
+    x, types = sc["x"], sc["types"]
+    p = _mix_params(sc)
+    et, st, rt = scenarios.perturbed_pair_params(sc["eps"], sc["sigma"])
+    Fstar = oracle.forces_cells(x, types, _mix_params(sc, et, st, rt), lib=lib)["F"]
+    pairs = oracle.forces_cells(x, types, p, pairs=True, lib=lib)["pairs"]
+    L, gx, ge, gs = oracle.force_loss_grad(x, types, p, Fstar, pairs=pairs, lib=lib)
+    loss = lambda xx, pp: oracle.force_loss(oracle.forces_list(xx, types, pp, pairs, lib=lib), Fstar)
+    th = _theta_vals(sc)
+    fd = [(loss(x, _theta_params(sc, sc["eps"], sc["sigma"], k, h)) -
+           loss(x, _theta_params(sc, sc["eps"], sc["sigma"], k, -h))) / (2 * h * th[k]) for k in range(6)]
+    assert _rel(_theta_grad(ge, gs), fd) < 1e-6, (_theta_grad(ge, gs), fd)
+    rng = np.random.default_rng(13)
+    idx = [(int(i), int(d)) for i, d in zip(rng.choice(len(x), 64, replace=False), rng.integers(0, 3, 64))]
+    fdx, an = [], []
+    for i, d in idx:
+        xp, xm = x.copy(), x.copy()
+        xp[i, d] += h
+        xm[i, d] -= h
+        fdx.append((loss(xp, p) - loss(xm, p)) / (2 * h))
+        an.append(gx[i, d])
+    assert _rel(an, fdx) < 1e-6, _rel(an, fdx)
+
+
+def _rollout_case(nsteps):
+    sc = scenarios.jittered_mixture(nside=7)
+    p = _mix_params(sc)
+    et, st, rt = scenarios.perturbed_pair_params(sc["eps"], sc["sigma"])
+    return sc, p, _mix_params(sc, et, st, rt)
+
+
+def pin_rollout_finite_difference(lib, nsteps=50, h=1e-6):
+    """Gradient of L = mean |F(x_N) - F*_N|^2 through N Verlet steps vs central
+    differences of reruns with every time level's mask frozen."""
+    sc, p, pt = _rollout_case(nsteps)
+    x0, v0, types, mass, dt = sc["x"], sc["v"], sc["types"], sc["mass"], sc["dt"]
+    xs_t, *_ = oracle.rollout(x0, v0, types, mass, pt, dt, nsteps, lib=lib)
+    FstarN = oracle.forces_cells(xs_t[nsteps], types, pt, lib=lib)["F"]
+    L, gx0, gv0, ge, gs = oracle.rollout_loss_grad(x0, v0, types, mass, p, dt, nsteps, FstarN, lib=lib)
+    _, _, masks, off = oracle.rollout(x0, v0, types, mass, p, dt, nsteps, lib=lib)
+    mN = masks[off[nsteps]:off[nsteps + 1]]
+
+    def loss(xx, vv, pp):
+        xs, *_ = oracle.rollout(xx, vv, types, mass, pp, dt, nsteps, frozen=(masks, off), lib=lib)
+        return oracle.force_loss(oracle.forces_list(xs[nsteps], types, pp, mN, lib=lib), FstarN)
+
+    assert abs(loss(x0, v0, p) - L) < 1e-14 * abs(L)
+    th = _theta_vals(sc)
+    fd = [(loss(x0, v0, _theta_params(sc, sc["eps"], sc["sigma"], k, h)) -
+           loss(x0, v0, _theta_params(sc, sc["eps"], sc["sigma"], k, -h))) / (2 * h * th[k]) for k in range(6)]
+    assert _rel(_theta_grad(ge, gs), fd) < 1e-6, (_theta_grad(ge, gs), fd)
+    rng = np.random.default_rng(14)
+    for which, g in (("x", gx0), ("v", gv0)):
+        fdx, an = [], []
+        for i, d in zip(rng.choice(len(x0), 12, replace=False), rng.integers(0, 3, 12)):
+            xp, xm, vp, vm = x0.copy(), x0.copy(), v0.copy(), v0.copy()
+            (xp if which == "x" else vp)[i, d] += h
+            (xm if which == "x" else vm)[i, d] -= h
+            fdx.append((loss(xp, vp, p) - loss(xm, vm, p)) / (2 * h))
+            an.append(g[i, d])
+        assert _rel(an, fdx) < 1e-6, (which, _rel(an, fdx))
+
+
+def pin_rollout_symplectic(lib, nsteps=10):
+    """The Verlet map is symplectic (unit masses), so is its transpose:
+    omega(J^T a, J^T b) = omega(a, b) with omega((x1, v1), (x2, v2)) =
+    x1.v2 - v1.x2; zero steps give the identity."""
+    sc, p, _ = _rollout_case(nsteps)
+    x0, v0, types, dt = sc["x"], sc["v"], sc["types"], sc["dt"]
+    rng = np.random.default_rng(15)
+    a = rng.normal(size=(2,) + x0.shape)
+    b = rng.normal(size=(2,) + x0.shape)
+    om = lambda u, w: float((u[0] * w[1]).sum() - (u[1] * w[0]).sum())
+    ta = oracle.rollout_vjp(x0, v0, types, [1.0, 1.0], p, dt, nsteps, a[0], a[1], lib=lib)[:2]
+    tb = oracle.rollout_vjp(x0, v0, types, [1.0, 1.0], p, dt, nsteps, b[0], b[1], lib=lib)[:2]
+    assert abs(om(ta, tb) - om(a, b)) < 1e-10 * np.sqrt(abs(om(ta, ta)) + om(a, b) ** 2 + 1.0), (om(ta, tb), om(a, b))
+    assert np.abs(ta[0] - a[0]).max() > 1e-6  # the map is not the identity
+    gx, gv, ge, gs = oracle.rollout_vjp(x0, v0, types, [1.0, 1.0], p, dt, 0, a[0], a[1], lib=lib)
+    assert np.array_equal(gx, a[0]) and np.array_equal(gv, a[1]) and not ge.any() and not gs.any()
+
+
 ALL_PINS = [pin_lj_minimum, pin_lj_shift, pin_lj_scaling_and_gradient, pin_two_body, pin_fcc_lattice,
             pin_newton3, pin_virial, pin_traversals_agree, pin_drifted_positions, pin_nve,
-            pin_reversibility, pin_bin_stats]
+            pin_reversibility, pin_bin_stats, pin_vjp_two_body, pin_vjp_invariants,
+            pin_vjp_finite_difference, pin_rollout_finite_difference, pin_rollout_symplectic]

@@ -34,6 +34,18 @@ MUTANTS = {
     "verlet_drift_half": ("x[3*i+d] += dt * v[3*i+d];", "x[3*i+d] += 0.5 * dt * v[3*i+d];"),
     "stats_variance_not_rooted": ("out[1] = mean > 0.0 ? sqrt(var) / mean : 0.0;", "out[1] = mean > 0.0 ? var / mean : 0.0;"),
     "stats_median_upper": ("0.5 * ((double)cnt[nb / 2 - 1] + (double)cnt[nb / 2])", "(double)cnt[nb / 2]"),
+    "list_newton3_sign": ("F[3*j+d] -= f * r[d];", "F[3*j+d] += f * r[d];"),
+    "vjp_dropped_radial_term": ("double w = g * u[d] + 2.0 * dgds * ur * r[d];", "double w = g * u[d] + dgds * ur * r[d];"),
+    "vjp_j_sign": ("gx[3*j+d] -= w;", "gx[3*j+d] += w;"),
+    "vjp_cotangent_transposed": ("u[d] = c[3*i+d] - c[3*j+d];", "u[d] = c[3*j+d] - c[3*i+d];"),
+    "vjp_dgds_power": ("4.0 * sig6 / s5);", "4.0 * sig6 / s4);"),
+    "vjp_dgdsig_factor": ("(24.0 * sig11 / s7 - 6.0 * sig5 / s4)", "(12.0 * sig11 / s7 - 6.0 * sig5 / s4)"),
+    "vjp_symmetric_entry_missing": ("gsig[b * nt + a] += ur * dgdsig;", "gsig[b * nt + a] += 0.0;"),
+    "rollout_drift_half": ("x[3*i+d] += dt * v[3*i+d];\n            }\n    }\n    free(x); free(v); free(F);",
+                           "x[3*i+d] += 0.5 * dt * v[3*i+d];\n            }\n    }\n    free(x); free(v); free(F);"),
+    "rollout_vjp_drift_coefficient": ("gv0[k] += dt * gx0[k];", "gv0[k] += 0.5 * dt * gx0[k];"),
+    "rollout_vjp_kick_levels_swapped": ("xs + (size_t)(t + level) * n3", "xs + (size_t)(t + 1 - level) * n3"),
+    "rollout_vjp_full_kick": ("cot[3*i+d] = 0.5 * dt / mass[type[i]] * gv0[3*i+d];", "cot[3*i+d] = dt / mass[type[i]] * gv0[3*i+d];"),
 }
 
 RUNNER = textwrap.dedent("""
