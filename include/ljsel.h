@@ -273,6 +273,60 @@ ljsel_status ljsel_profile_steps(ljsel_system s, int64_t nsteps, ljsel_profile *
  * returns their number in *count.                                         */
 ljsel_status ljsel_default_candidates(ljsel_system s, int32_t cap, ljsel_config *out, int32_t *count);
 
+/* ---- Gradients --------------------------------------------------------
+ * The paper has no gradient; these calls serve the differentiable binary
+ * mixture (a force-matching loss differentiated with respect to positions
+ * and the per-type-pair eps/sigma).  Definitions:
+ *  - F_i = sum_j g(r_ij^2) r_ij over the in-range pairs, r_ij = x_i - x_j
+ *    (minimum image), g(s) = 24 eps (2 sig^12 / s^7 - sig^6 / s^4)
+ *    (Sec. 2.1 names the LJ potential; the energy shift does not enter F).
+ *  - The pair set is frozen at the evaluation point: derivatives are those
+ *    of the fixed sum over the pairs in range there (the cutoff's motion
+ *    with sigma and the jump of F at r_c are not differentiated).
+ *  - eps_ab = eps_ba is one parameter; gradient entries (a,b) and (b,a)
+ *    both hold the derivative with respect to it.
+ * Arithmetic is in the system's precision (FP32 pair math with FP64 sums,
+ * or FP64 throughout with precision 1).                                   */
+
+/* Replace the per-type-pair tables (ntypes x ntypes each, row-major,
+ * symmetric; eps >= 0, sigma > 0).  rcut NULL keeps the current cutoffs.
+ * Positions and velocities are kept; the neighbour structure is rebuilt
+ * before the next evaluation (and the cell grid re-planned if the largest
+ * cutoff changed).  Invalidates a recorded rollout.  Errors: ARG for
+ * invalid tables, BOX when the new cutoffs no longer fit the box.        */
+ljsel_status ljsel_set_pair_params(ljsel_system s, const double *eps, const double *sigma, const double *rcut);
+
+/* Vector-Jacobian product of the forces at the current working positions:
+ *   cot   (host or device, n x 3): the cotangent dL/dF, input order;
+ *   g_pos (host or device, n x 3, or NULL): (dF/dx)^T cot, i.e. minus the
+ *         Hessian of the potential energy applied to cot;
+ *   g_eps, g_sigma (host, ntypes x ntypes each, or NULL): d(cot . F)/d eps
+ *         and d(cot . F)/d sigma.
+ * Synchronizes the stream.                                                */
+ljsel_status ljsel_force_vjp(ljsel_system s, const double *cot, int32_t on_device, double *g_pos,
+                             double *g_eps, double *g_sigma);
+
+/* Advance nsteps Stormer-Verlet steps (as ljsel_step) while recording the
+ * state at steps 0, every, 2 every, ... (checkpoints in device memory owned
+ * by the system, 48 bytes per particle each) and at the end.  At every
+ * checkpoint the neighbour structure is rebuilt from the recorded state, so
+ * that ljsel_rollout_vjp can recompute each segment bit for bit.  The
+ * system ends at step nsteps with velocities at the integer step, as after
+ * ljsel_set_state.  Errors: ARG for nsteps < 0 or every < 1.             */
+ljsel_status ljsel_rollout(ljsel_system s, int64_t nsteps, int64_t every);
+
+/* Reverse-mode derivative of the last ljsel_rollout: from the cotangents
+ * xbar, vbar (host or device, n x 3, input order; vbar may be NULL = 0) of
+ * the final positions and velocities, the cotangents of the initial ones
+ * (g_x0, g_v0: host or device, n x 3, or NULL) and of eps/sigma (g_eps,
+ * g_sigma: host, ntypes x ntypes, or NULL).  Each segment between
+ * checkpoints is recomputed forward and then reversed level by level, one
+ * force VJP per time level.  The system is left at the rollout's final
+ * state.  Errors: STATE when no rollout was recorded, or the configuration
+ * or parameters changed since.  Synchronizes the stream.                 */
+ljsel_status ljsel_rollout_vjp(ljsel_system s, const double *xbar, const double *vbar, int32_t on_device,
+                               double *g_x0, double *g_v0, double *g_eps, double *g_sigma);
+
 /* Allocation-free force evaluation.  The paper has no counterpart: this is
  * a service for callers that cannot allocate device memory -- code running
  * while a stream is captured into a CUDA graph, code inside a framework

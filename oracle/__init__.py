@@ -275,12 +275,13 @@ def force_vjp(x, types, params: Params, pairs, cot, lib=None):
     return gx, ge.reshape(nt, nt), gs.reshape(nt, nt)
 
 
-def rollout(x0, v0, types, mass, params: Params, dt, nsteps, frozen=None, lib=None):
+def rollout(x0, v0, types, mass, params: Params, dt, nsteps, frozen=None, record_masks=True, lib=None):
     """Unwrapped velocity-form Stormer-Verlet (Sec. 2.1) for gradient checks.
 
     Returns (xs [nsteps+1, n, 3], vs [...], masks, offsets): with ``frozen``
     = (masks, offsets) of an earlier run the pair mask of every time level is
-    taken from it instead of being recomputed.
+    taken from it instead of being recomputed; without ``record_masks`` the
+    masks are not kept (masks, offsets are None).
     """
     lib = lib or load()
     x0, types, n = _prep(x0, types)
@@ -293,9 +294,13 @@ def rollout(x0, v0, types, mass, params: Params, dt, nsteps, frozen=None, lib=No
         lib.orc_rollout(n, _dp(x0), _dp(v0), _ip(types), _dp(mass), ctypes.byref(params), float(dt), int(nsteps),
                         _dp(xs), _dp(vs), _ip(masks), off.ctypes.data_as(_I64), None, 0, None)
         return xs, vs, masks, off
+    if not record_masks:
+        lib.orc_rollout(n, _dp(x0), _dp(v0), _ip(types), _dp(mass), ctypes.byref(params), float(dt), int(nsteps),
+                        _dp(xs), _dp(vs), None, None, None, 0, None)
+        return xs, vs, None, None
     off = np.zeros(nsteps + 2, np.int64)
-    cap = 0
-    masks = np.zeros((1, 2), np.int32)
+    cap = int(forces_cells(x0, types, params, lib=lib)["count"] * 1.25 * (nsteps + 1)) + 1024
+    masks = np.zeros((cap, 2), np.int32)
     for _ in range(2):
         total = lib.orc_rollout(n, _dp(x0), _dp(v0), _ip(types), _dp(mass), ctypes.byref(params), float(dt),
                                 int(nsteps), _dp(xs), _dp(vs), None, None, _ip(masks), cap,
@@ -347,8 +352,7 @@ def force_loss_grad(x, types, params: Params, Fstar, pairs=None, lib=None):
 def rollout_loss_grad(x0, v0, types, mass, params: Params, dt, nsteps, Fstar_end, lib=None):
     """L = mean |F(x_N) - F*|^2 after N steps, and its gradient w.r.t. x_0, v_0, eps, sigma."""
     lib = lib or load()
-    xs, _, masks, off = rollout(x0, v0, types, mass, params, dt, nsteps, lib=lib)
-    pe = masks[off[nsteps]:off[nsteps + 1]]
-    L, gxN, ge1, gs1 = force_loss_grad(xs[nsteps], types, params, Fstar_end, pairs=pe, lib=lib)
+    xs, *_ = rollout(x0, v0, types, mass, params, dt, nsteps, record_masks=False, lib=lib)
+    L, gxN, ge1, gs1 = force_loss_grad(xs[nsteps], types, params, Fstar_end, lib=lib)
     gx0, gv0, ge2, gs2 = rollout_vjp(x0, v0, types, mass, params, dt, nsteps, gxN, np.zeros_like(gxN), lib=lib)
     return L, gx0, gv0, ge1 + ge2, gs1 + gs2

@@ -528,6 +528,10 @@ int64_t orc_rollout(int64_t n, const double *x0, const double *v0, const int32_t
         /* forces at x_t */
         if (frozen) {
             orc_forces_list(n, x, type, p, frozen + 2 * off[t], off[t+1] - off[t], F);
+        } else if (!masks_out && !off_out) {
+            double rcmax = 0.0;
+            for (int k = 0; k < p->ntypes * p->ntypes; ++k) if (p->rcut[k] > rcmax) rcmax = p->rcut[k];
+            orc_forces_cells(n, x, type, p, rcmax, 0, F, NULL, NULL, NULL, 0);
         } else {
             int64_t np;
             int32_t *pr = pairs_at(n, x, type, p, F, &np);

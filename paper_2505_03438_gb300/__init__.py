@@ -147,6 +147,10 @@ _SIGS = {
     "ljsel_profile_steps": ([_P, ctypes.c_int64, ctypes.POINTER(ljsel_profile)], ctypes.c_int),
     "ljsel_default_candidates": ([_P, ctypes.c_int32, ctypes.POINTER(ljsel_config), ctypes.POINTER(ctypes.c_int32)],
                                  ctypes.c_int),
+    "ljsel_set_pair_params": ([_P, _P, _P, _P], ctypes.c_int),
+    "ljsel_force_vjp": ([_P, _P, ctypes.c_int32, _P, _P, _P], ctypes.c_int),
+    "ljsel_rollout": ([_P, ctypes.c_int64, ctypes.c_int64], ctypes.c_int),
+    "ljsel_rollout_vjp": ([_P, _P, _P, ctypes.c_int32, _P, _P, _P, _P], ctypes.c_int),
 }
 EXPORTED = tuple(_SIGS)
 _lib = None
@@ -373,6 +377,49 @@ def ljsel_autotune(h, strategy=0, trial_steps=10, predict_factor=2.0, blacklist_
     return chosen, {k: getattr(rep, k) for k, _ in rep._fields_}
 
 
+def _table(a, nt):
+    a = np.ascontiguousarray(np.broadcast_to(np.asarray(a, np.float64), (nt, nt)))
+    return a
+
+
+def ljsel_set_pair_params(h, eps, sigma, rcut=None):
+    """Replace the ntypes x ntypes eps/sigma (and optionally rcut) tables."""
+    eps = np.ascontiguousarray(np.atleast_2d(np.asarray(eps, np.float64)))
+    nt = eps.shape[0]
+    sigma = _table(sigma, nt)
+    rc = None if rcut is None else _table(rcut, nt)
+    _check(lib().ljsel_set_pair_params(h, eps.ctypes.data, sigma.ctypes.data, None if rc is None else rc.ctypes.data))
+
+
+def ljsel_force_vjp(h, cot, g_pos=None, ntypes=1):
+    """(dF/dx)^T cot into g_pos (same residency as cot); returns (g_eps, g_sigma) as ntypes x ntypes arrays."""
+    cp, d1 = _ptr(cot)
+    gp, d2 = _ptr(g_pos)
+    if g_pos is not None and d1 != d2:
+        raise ValueError("cot and g_pos must be both host or both device")
+    ge = np.zeros((ntypes, ntypes))
+    gs = np.zeros((ntypes, ntypes))
+    _check(lib().ljsel_force_vjp(h, cp, d1, gp, ge.ctypes.data, gs.ctypes.data))
+    return ge, gs
+
+
+def ljsel_rollout(h, nsteps, every):
+    _check(lib().ljsel_rollout(h, int(nsteps), int(every)))
+
+
+def ljsel_rollout_vjp(h, xbar, vbar=None, g_x0=None, g_v0=None, ntypes=1):
+    """Cotangents of (x_0, v_0) into g_x0/g_v0 (same residency as xbar); returns (g_eps, g_sigma)."""
+    xp, d = _ptr(xbar)
+    for a in (vbar, g_x0, g_v0):
+        if a is not None and _ptr(a)[1] != d:
+            raise ValueError("xbar, vbar, g_x0 and g_v0 must share one residency")
+    ge = np.zeros((ntypes, ntypes))
+    gs = np.zeros((ntypes, ntypes))
+    _check(lib().ljsel_rollout_vjp(h, xp, _ptr(vbar)[0], d, _ptr(g_x0)[0], _ptr(g_v0)[0], ge.ctypes.data,
+                                   gs.ctypes.data))
+    return ge, gs
+
+
 class System:
     """Owner of one ljsel handle (destroyed with the object); marshalling only."""
 
@@ -405,6 +452,7 @@ class System:
 
     def set_config(self, cfg=None, **kw):
         ljsel_set_config(self.h, cfg if cfg is not None else make_config(**kw))
+        self._rollout_valid = False
 
     def config(self):
         return ljsel_get_config(self.h)
@@ -455,3 +503,43 @@ class System:
 
     def rebuild(self):
         ljsel_rebuild(self.h)
+
+    @property
+    def ntypes(self):
+        return int(self.params.ntypes)
+
+    def set_pair_params(self, eps, sigma, rcut=None):
+        nt = self.ntypes
+        tab = lambda a: np.broadcast_to(np.asarray(a, np.float64), (nt, nt)).reshape(-1)
+        new = [(self.params.eps, tab(eps)), (self.params.sigma, tab(sigma))]
+        if rcut is not None:
+            new.append((self.params.rcut, tab(rcut)))
+        ljsel_set_pair_params(self.h, eps, sigma, rcut)
+        changed = False
+        for dst, src in new:
+            for k in range(nt * nt):
+                changed |= dst[k] != float(src[k])
+                dst[k] = float(src[k])
+        if changed:
+            self._rollout_valid = False  # the library dropped its rollout record
+
+    def has_rollout(self):
+        return getattr(self, "_rollout_valid", False)
+
+    def force_vjp(self, cot):
+        """Returns (g_pos, g_eps, g_sigma) for a host cotangent (n x 3)."""
+        g = np.zeros((self.n, 3))
+        ge, gs = ljsel_force_vjp(self.h, np.ascontiguousarray(cot, np.float64), g, self.ntypes)
+        return g, ge, gs
+
+    def rollout(self, nsteps, every):
+        ljsel_rollout(self.h, nsteps, every)
+        self._rollout_valid = True
+
+    def rollout_vjp(self, xbar, vbar=None):
+        """Returns (g_x0, g_v0, g_eps, g_sigma) for host cotangents of the final state."""
+        gx = np.zeros((self.n, 3))
+        gv = np.zeros((self.n, 3))
+        vb = None if vbar is None else np.ascontiguousarray(vbar, np.float64)
+        ge, gs = ljsel_rollout_vjp(self.h, np.ascontiguousarray(xbar, np.float64), vb, gx, gv, self.ntypes)
+        return gx, gv, ge, gs

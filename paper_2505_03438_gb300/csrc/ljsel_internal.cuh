@@ -69,6 +69,7 @@ template <typename R> struct PairTab {
     R sig2[MAXT2], e24[MAXT2], e48[MAXT2], e4[MAXT2], ushift[MAXT2];
     R rc2lo[MAXT2], rc2hi[MAXT2];
     double rc2d[MAXT2];
+    R inv_sig[MAXT2];      // 1 / sigma (parameter derivatives)
     R inv_mass_dt[MAXT];   // dt / m per type
     double dt;
     double half_mass[MAXT];

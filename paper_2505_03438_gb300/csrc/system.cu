@@ -144,7 +144,8 @@ std::vector<Buf *> System::all_bufs() {
     return {&b_x[0], &b_x[1], &b_v[0], &b_v[1], &b_id[0], &b_id[1], &b_type[0], &b_type[1], &b_pos[0], &b_pos[1],
             &b_xref, &b_force, &b_cell_count, &b_cell_start, &b_clcell_start, &b_cell_of, &b_slot_of, &b_key_of,
             &b_tmp_idx, &b_tmp_key, &b_cell_sorted, &b_scan, &b_nl, &b_nl_count, &b_strips, &b_nstrips, &b_cl_first, &b_cl_count,
-            &b_cl_cell, &b_cl_lo, &b_cl_hi, &b_cp, &b_cp_count, &b_ncl, &b_ctrl, &b_io};
+            &b_cl_cell, &b_cl_lo, &b_cl_hi, &b_cp, &b_cp_count, &b_ncl, &b_ctrl, &b_io,
+            &b_adj_cot, &b_adj_x, &b_adj_v, &b_adj_theta, &b_ckpt, &b_seg};
 }
 
 void System::drop_graph() {
@@ -352,6 +353,7 @@ template <typename R> void System::fill_dev(Dev<R> &S) const {
             const double sr = sg / rc, sr6 = sr * sr * sr * sr * sr * sr;
             const double uc = 4.0 * e * (sr6 * sr6 - sr6);
             S.tab.sig2[t] = (R)(sg * sg);
+            S.tab.inv_sig[t] = (R)(1.0 / sg);
             S.tab.e24[t] = (R)(24.0 * e);
             S.tab.e48[t] = (R)(48.0 * e);
             S.tab.e4[t] = (R)(4.0 * e);

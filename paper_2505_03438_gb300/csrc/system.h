@@ -66,6 +66,14 @@ struct System {
     Buf b_nl, b_nl_count, b_strips, b_nstrips;
     Buf b_cl_first, b_cl_count, b_cl_cell, b_cl_lo, b_cl_hi, b_cp, b_cp_count, b_ncl;
     Buf b_ctrl, b_io;
+    // gradients: sorted cotangent, caller-order adjoint state, parameter
+    // sums, rollout checkpoints and the recomputed segment
+    Buf b_adj_cot, b_adj_x, b_adj_v, b_adj_theta, b_ckpt, b_seg;
+    struct Rollout {
+        long long nsteps = -1, every = 0;
+        ljsel_config cfg{};
+        ljsel_params params{};
+    } rollout;
     Ctrl *h_ctrl = nullptr;  // pinned mirror
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     // step graphs, one per (configuration, device layout); gexec is the

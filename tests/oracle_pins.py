@@ -390,7 +390,7 @@ def pin_rollout_finite_difference(lib, nsteps=50, h=1e-6):
     differences of reruns with every time level's mask frozen."""
     sc, p, pt = _rollout_case(nsteps)
     x0, v0, types, mass, dt = sc["x"], sc["v"], sc["types"], sc["mass"], sc["dt"]
-    xs_t, *_ = oracle.rollout(x0, v0, types, mass, pt, dt, nsteps, lib=lib)
+    xs_t, *_ = oracle.rollout(x0, v0, types, mass, pt, dt, nsteps, record_masks=False, lib=lib)
     FstarN = oracle.forces_cells(xs_t[nsteps], types, pt, lib=lib)["F"]
     L, gx0, gv0, ge, gs = oracle.rollout_loss_grad(x0, v0, types, mass, p, dt, nsteps, FstarN, lib=lib)
     _, _, masks, off = oracle.rollout(x0, v0, types, mass, p, dt, nsteps, lib=lib)
