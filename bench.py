@@ -122,6 +122,50 @@ def oracle_rate(sc, budget_s=12.0):
                       (nsteps, n, cores)}
 
 
+def adjoint_leg(reps=20, nsteps=50, every=10):
+    """Gradient workload (differentiable binary mixture, N = 32,768, FP32 pair
+    math): wall time per call through the C ABI with device buffers, each
+    call synchronising -- forces, force VJP, a 50-step checkpointed rollout
+    and its reverse pass."""
+    import numpy as np
+    import torch
+
+    import paper_2505_03438_gb300 as lj
+    from paper_2505_03438_gb300 import scenarios
+
+    sc = scenarios.binary_mixture()
+    s = lj.System(sc, precision=0, stream=torch.cuda.current_stream().cuda_stream)
+    n = s.n
+    F = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    cot = torch.randn((n, 3), dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(7))
+    g = torch.empty_like(F)
+
+    def per_call(fn, k):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k):
+            fn()
+        torch.cuda.synchronize()
+        return 1e3 * (time.perf_counter() - t0) / k
+
+    out = {"workload": "binary_32768: KA-type 80:20 mixture, rho 1.2, rc 2.5 sigma_ab, FP32 pair math",
+           "force_call_ms": per_call(lambda: lj.ljsel_compute(s.h, F), reps),
+           "vjp_call_ms": per_call(lambda: lj.ljsel_force_vjp(s.h, cot, g, s.ntypes), reps)}
+    xb = torch.randn((n, 3), dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(8))
+    gx, gv = torch.empty_like(xb), torch.empty_like(xb)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lj.ljsel_rollout(s.h, nsteps, every)
+    t1 = time.perf_counter()
+    lj.ljsel_rollout_vjp(s.h, xb, None, gx, gv, s.ntypes)
+    t2 = time.perf_counter()
+    out.update({"rollout_steps": nsteps, "checkpoint_every": every, "rollout_ms": 1e3 * (t1 - t0),
+                "rollout_vjp_ms": 1e3 * (t2 - t1), "pairs_within_cutoff": s.pairs()[1]})
+    s.close()
+    return out
+
+
 def run_reference(args):
     """Reference arm: the oracle as it stands, on the host cores."""
     from paper_2505_03438_gb300 import scenarios
@@ -300,6 +344,7 @@ def run_ours(args):
     cb = None
     if args.cpu_baseline and world == 1:
         cb = oracle_rate(sc)
+    adj = adjoint_leg() if args.adjoint else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": int(steps_done),
         "warmup": W, "ms_per_step": ms / max(steps_done, 1), "higher_is_better": True, "scaling": "weak",
@@ -321,6 +366,7 @@ def run_ours(args):
         "other_tuned_runs": extra_runs,
         "fixed": fixed,
         "best_fixed": max(fixed.items(), key=lambda kv: kv[1]) if fixed else None,
+        "adjoint": adj,
     }
     # kernels launched in the timed region: per step the force (and update
     # when N3L is on) and the control kernel, per rebuild its chain, plus the
@@ -354,6 +400,7 @@ def main():
     ap.add_argument("--eager", action="store_true", help="plain stream launches instead of the step graph")
     ap.add_argument("--no-other", dest="other", action="store_false", help="skip the second tuning strategy")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-adjoint", dest="adjoint", action="store_false", help="skip the gradient-workload timings")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -76,19 +76,29 @@ __global__ void k_adj_cot(Dev<R> S, const double *src, double *vbar, const doubl
     cot[k] = make_pos((R)(c * v[0]), (R)(c * v[1]), (R)(c * v[2]), 0);
 }
 
-// One thread per particle i (sorted order) over the stencil cells, the same
+// A group of G lanes per particle i (sorted order) over the stencil cells,
+// the lanes of a group taking every G-th candidate of each cell; the same
 // traversal and the same cutoff decision as the linked-cell force kernel.
+// G grows as the system shrinks so that the grid fills the GPU.
 // gx (caller order) receives (accumulate ? += : =) the position gradient;
 // theta[0..MAXT2) and theta[MAXT2..2 MAXT2) receive the eps and sigma sums
 // per ordered type pair (type_i, type_j).
-template <typename R>
+template <typename R, int G>
+__device__ __forceinline__ R group_sum(R v) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename R, int G>
 __global__ void __launch_bounds__(VJP_THREADS) k_vjp(Dev<R> S, const V4<R> *cot, double *gx, int accumulate,
                                                     double *theta) {
     __shared__ double red[2 * MAXT2];
     for (int k = threadIdx.x; k < 2 * MAXT2; k += blockDim.x) red[k] = 0.0;
     __syncthreads();
     const Ctrl *C = S.ctrl;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = gid / G, sub = gid % G;
     const bool valid = i < S.n;
     const int pp = C->pos_par, sp = C->state_par, nt = S.tab.ntypes;
     const V4<R> *P = S.pos[pp];
@@ -116,7 +126,7 @@ __global__ void __launch_bounds__(VJP_THREADS) k_vjp(Dev<R> S, const V4<R> *cot,
                     const int cc = (wz * S.nc[1] + wy) * S.nc[0] + wx;
                     const bool img = (sx | sy | sz) != 0;
                     const int jb = S.cell_start[cc], je = S.cell_start[cc + 1];
-                    for (int j = jb; j < je; ++j) {
+                    for (int j = jb + sub; j < je; j += G) {
                         if (!img && j == i) continue;
                         const V4<R> pj = ldpos(P, j);
                         R dx, dy, dz;
@@ -157,6 +167,16 @@ __global__ void __launch_bounds__(VJP_THREADS) k_vjp(Dev<R> S, const V4<R> *cot,
                 }
             }
         }
+    }
+    gxx = group_sum<R, G>(gxx);
+    gxy = group_sum<R, G>(gxy);
+    gxz = group_sum<R, G>(gxz);
+#pragma unroll
+    for (int k = 0; k < MAXT; ++k) {
+        ge[k] = group_sum<R, G>(ge[k]);
+        gs[k] = group_sum<R, G>(gs[k]);
+    }
+    if (valid && sub == 0) {
         const int id = S.id[sp][i];
         if (accumulate) {
             gx[3 * id + 0] += (double)gxx; gx[3 * id + 1] += (double)gxy; gx[3 * id + 2] += (double)gxz;
@@ -216,8 +236,19 @@ ljsel_status vjp_level(System *s, const double *src, double *vbar, const double 
     s->fill_dev(S);
     V4<R> *cot = (V4<R> *)s->b_adj_cot.ptr;
     k_adj_cot<R><<<div_up(s->n + 1, 256), 256, 0, s->stream>>>(S, src, vbar, xbar, dt_x, co, cot);
-    k_vjp<R><<<div_up(s->n, VJP_THREADS), VJP_THREADS, 0, s->stream>>>(S, cot, gx, accumulate,
-                                                                         (double *)s->b_adj_theta.ptr);
+    double *th = (double *)s->b_adj_theta.ptr;
+    // lanes per particle: enough threads for 152 SMs x 2048 resident threads
+    int G = 1;
+    while (G < 32 && (long long)s->n * G < 152LL * 2048) G *= 2;
+    const int grid = div_up((long long)s->n * G, VJP_THREADS);
+    switch (G) {
+        case 1: k_vjp<R, 1><<<grid, VJP_THREADS, 0, s->stream>>>(S, cot, gx, accumulate, th); break;
+        case 2: k_vjp<R, 2><<<grid, VJP_THREADS, 0, s->stream>>>(S, cot, gx, accumulate, th); break;
+        case 4: k_vjp<R, 4><<<grid, VJP_THREADS, 0, s->stream>>>(S, cot, gx, accumulate, th); break;
+        case 8: k_vjp<R, 8><<<grid, VJP_THREADS, 0, s->stream>>>(S, cot, gx, accumulate, th); break;
+        case 16: k_vjp<R, 16><<<grid, VJP_THREADS, 0, s->stream>>>(S, cot, gx, accumulate, th); break;
+        default: k_vjp<R, 32><<<grid, VJP_THREADS, 0, s->stream>>>(S, cot, gx, accumulate, th); break;
+    }
     CK(cudaGetLastError());
     return LJSEL_OK;
 }
