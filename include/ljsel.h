@@ -327,6 +327,61 @@ ljsel_status ljsel_rollout(ljsel_system s, int64_t nsteps, int64_t every);
 ljsel_status ljsel_rollout_vjp(ljsel_system s, const double *xbar, const double *vbar, int32_t on_device,
                                double *g_x0, double *g_v0, double *g_eps, double *g_sigma);
 
+/* ---- Batched replicas ---------------------------------------------------
+ * Many independent periodic single-species LJ systems of uneven size, each
+ * in its own box with its own cell grid (Sec. 2.2.1), stepped together: one
+ * launch per kernel stage covers all of them and a run of steps is one CUDA
+ * graph.  All replicas share eps, sigma, r_c, the shift, mass, skin, dt and
+ * precision.  The rebuild rule is the single system's, taken over the whole
+ * batch: every R steps, or as soon as any particle moved skin/2.
+ * Particle arrays are the replicas' arrays concatenated in replica order
+ * (sum(counts) x 3 doubles); the library keeps that order for the caller.  */
+typedef struct ljsel_batch_s *ljsel_batch;
+
+/* Shape of the batched force kernel: lanes per particle, threads per CTA,
+ * and 0 (one lane group per particle) or the CTAs per SM of a persistent
+ * grid that strides over the particles.  rebuild_interval = R.           */
+typedef struct ljsel_batch_tile {
+    int32_t threads_per_particle;  /* 1, 2, 4, 8                             */
+    int32_t block_threads;         /* 64, 128, 256                           */
+    int32_t persistent_ctas_per_sm;/* 0 .. 32                                */
+    int32_t rebuild_interval;      /* >= 1 (1 without a skin)                */
+} ljsel_batch_tile;
+
+/* Create a batch.  params: shared parameters (ntypes must be 1; box is
+ * ignored).  boxes: host, nrep x 3; counts: host, nrep (>= 0 each, total in
+ * [1, 2^27)); pos, vel: host or device, sum(counts) x 3.  Errors: ARG, BOX
+ * (a replica box below 2 (r_c + skin)), UNSUPPORTED (ntypes > 1), OOM.    */
+ljsel_status ljsel_batch_create(const ljsel_params *params, int32_t nrep, const double *boxes, const int64_t *counts,
+                                const double *pos, const double *vel, int32_t on_device, void *stream,
+                                ljsel_batch *out);
+ljsel_status ljsel_batch_destroy(ljsel_batch b);
+ljsel_status ljsel_batch_set_tile(ljsel_batch b, const ljsel_batch_tile *tile);
+ljsel_status ljsel_batch_get_tile(ljsel_batch b, ljsel_batch_tile *tile);
+/* Advance every replica nsteps steps (one CUDA graph; _eager: plain stream
+ * launches, bit-identical results).                                       */
+ljsel_status ljsel_batch_step(ljsel_batch b, int64_t nsteps);
+ljsel_status ljsel_batch_step_eager(ljsel_batch b, int64_t nsteps);
+/* Forces (host or device, sum(counts) x 3) at the current positions, and
+ * per-replica potential energy and virial (host, nrep each; NULL to skip).
+ * Synchronizes the stream.                                                */
+ljsel_status ljsel_batch_compute(ljsel_batch b, double *forces, int32_t on_device, double *energy, double *virial);
+/* Positions (wrapped into each replica's box) and integer-step velocities,
+ * host or device, sum(counts) x 3 each (either may be NULL).             */
+ljsel_status ljsel_batch_get_state(ljsel_batch b, double *pos, double *vel, int32_t on_device);
+/* The working-precision positions the pair arithmetic uses (host only).   */
+ljsel_status ljsel_batch_get_work_positions(ljsel_batch b, double *pos);
+/* In-range pairs: rij (host, 3 x cap) gets (replica, i, j) triples with i < j
+ * replica-local input indices; *count the total (may exceed cap).         */
+ljsel_status ljsel_batch_get_pairs(ljsel_batch b, int64_t cap, int32_t *rij, int64_t *count);
+ljsel_status ljsel_batch_get_counters(ljsel_batch b, ljsel_counters *c);
+/* Tile selection by full search: each candidate (ncand = 0: a default set
+ * of ten) runs trial_steps timed steps that advance the batch; the fastest
+ * per step is kept and returned in *chosen; costs_ms (host, ncand or ten
+ * entries, or NULL) receives each candidate's ms/step (-1: not run).     */
+ljsel_status ljsel_batch_autotune(ljsel_batch b, int32_t trial_steps, int32_t ncand, const ljsel_batch_tile *cand,
+                                  ljsel_batch_tile *chosen, double *costs_ms);
+
 /* Allocation-free force evaluation.  The paper has no counterpart: this is
  * a service for callers that cannot allocate device memory -- code running
  * while a stream is captured into a CUDA graph, code inside a framework

@@ -118,6 +118,14 @@ class ljsel_profile(ctypes.Structure):
                 ("control_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
 
 
+class ljsel_batch_tile(ctypes.Structure):
+    _fields_ = [("threads_per_particle", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+                ("persistent_ctas_per_sm", ctypes.c_int32), ("rebuild_interval", ctypes.c_int32)]
+
+    def as_tuple(self):
+        return (self.threads_per_particle, self.block_threads, self.persistent_ctas_per_sm, self.rebuild_interval)
+
+
 _P = ctypes.c_void_p
 _SIGS = {
     "ljsel_last_error": ([], ctypes.c_char_p),
@@ -151,6 +159,20 @@ _SIGS = {
     "ljsel_force_vjp": ([_P, _P, ctypes.c_int32, _P, _P, _P], ctypes.c_int),
     "ljsel_rollout": ([_P, ctypes.c_int64, ctypes.c_int64], ctypes.c_int),
     "ljsel_rollout_vjp": ([_P, _P, _P, ctypes.c_int32, _P, _P, _P, _P], ctypes.c_int),
+    "ljsel_batch_create": ([ctypes.POINTER(ljsel_params), ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int32, _P,
+                            ctypes.POINTER(_P)], ctypes.c_int),
+    "ljsel_batch_destroy": ([_P], ctypes.c_int),
+    "ljsel_batch_set_tile": ([_P, ctypes.POINTER(ljsel_batch_tile)], ctypes.c_int),
+    "ljsel_batch_get_tile": ([_P, ctypes.POINTER(ljsel_batch_tile)], ctypes.c_int),
+    "ljsel_batch_step": ([_P, ctypes.c_int64], ctypes.c_int),
+    "ljsel_batch_step_eager": ([_P, ctypes.c_int64], ctypes.c_int),
+    "ljsel_batch_compute": ([_P, _P, ctypes.c_int32, _P, _P], ctypes.c_int),
+    "ljsel_batch_get_state": ([_P, _P, _P, ctypes.c_int32], ctypes.c_int),
+    "ljsel_batch_get_work_positions": ([_P, _P], ctypes.c_int),
+    "ljsel_batch_get_pairs": ([_P, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "ljsel_batch_get_counters": ([_P, ctypes.POINTER(ljsel_counters)], ctypes.c_int),
+    "ljsel_batch_autotune": ([_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.POINTER(ljsel_batch_tile), _P],
+                             ctypes.c_int),
 }
 EXPORTED = tuple(_SIGS)
 _lib = None
@@ -543,3 +565,164 @@ class System:
         vb = None if vbar is None else np.ascontiguousarray(vbar, np.float64)
         ge, gs = ljsel_rollout_vjp(self.h, np.ascontiguousarray(xbar, np.float64), vb, gx, gv, self.ntypes)
         return gx, gv, ge, gs
+
+
+# --- batched replicas -----------------------------------------------------------
+
+def ljsel_batch_create(params: ljsel_params, boxes, counts, pos, vel, stream=None):
+    boxes = np.ascontiguousarray(boxes, np.float64).reshape(-1, 3)
+    counts = np.ascontiguousarray(counts, np.int64)
+    pp, d1 = _ptr(pos)
+    vp, d2 = _ptr(vel)
+    if d1 != d2:
+        raise ValueError("pos and vel must be both host or both device")
+    h = ctypes.c_void_p()
+    _check(lib().ljsel_batch_create(ctypes.byref(params), len(counts), boxes.ctypes.data, counts.ctypes.data, pp, vp,
+                                    d1, stream, ctypes.byref(h)))
+    return h
+
+
+def ljsel_batch_destroy(b):
+    _check(lib().ljsel_batch_destroy(b))
+
+
+def make_tile(threads_per_particle=1, block_threads=128, persistent_ctas_per_sm=0, rebuild_interval=10):
+    return ljsel_batch_tile(int(threads_per_particle), int(block_threads), int(persistent_ctas_per_sm),
+                            int(rebuild_interval))
+
+
+def ljsel_batch_set_tile(b, tile: ljsel_batch_tile):
+    _check(lib().ljsel_batch_set_tile(b, ctypes.byref(tile)))
+
+
+def ljsel_batch_get_tile(b) -> ljsel_batch_tile:
+    t = ljsel_batch_tile()
+    _check(lib().ljsel_batch_get_tile(b, ctypes.byref(t)))
+    return t
+
+
+def ljsel_batch_step(b, nsteps):
+    _check(lib().ljsel_batch_step(b, int(nsteps)))
+
+
+def ljsel_batch_step_eager(b, nsteps):
+    _check(lib().ljsel_batch_step_eager(b, int(nsteps)))
+
+
+def ljsel_batch_compute(b, forces=None, nrep=0):
+    """Forces into ``forces`` (host or device); returns per-replica (energy, virial) arrays."""
+    fp, d = _ptr(forces)
+    e = np.zeros(max(nrep, 1))
+    w = np.zeros(max(nrep, 1))
+    _check(lib().ljsel_batch_compute(b, fp, d, e.ctypes.data if nrep else None, w.ctypes.data if nrep else None))
+    return e[:nrep], w[:nrep]
+
+
+def ljsel_batch_get_state(b, pos=None, vel=None):
+    pp, d1 = _ptr(pos)
+    vp, d2 = _ptr(vel)
+    if pos is not None and vel is not None and d1 != d2:
+        raise ValueError("pos and vel must be both host or both device")
+    _check(lib().ljsel_batch_get_state(b, pp, vp, d1 if pos is not None else d2))
+
+
+def ljsel_batch_get_work_positions(b, pos):
+    p, d = _ptr(pos)
+    if d:
+        raise ValueError("work positions are returned to host memory")
+    _check(lib().ljsel_batch_get_work_positions(b, p))
+
+
+def ljsel_batch_get_pairs(b, cap):
+    buf = np.zeros((max(int(cap), 1), 3), np.int32)
+    cnt = ctypes.c_int64()
+    _check(lib().ljsel_batch_get_pairs(b, int(cap), buf.ctypes.data, ctypes.byref(cnt)))
+    return buf[:min(cnt.value, int(cap))], cnt.value
+
+
+def ljsel_batch_get_counters(b) -> dict:
+    c = ljsel_counters()
+    _check(lib().ljsel_batch_get_counters(b, ctypes.byref(c)))
+    return {k: getattr(c, k) for k, _ in c._fields_}
+
+
+def ljsel_batch_autotune(b, trial_steps=20, candidates=None):
+    """Full search over force-kernel tiles; returns (chosen tile, list of (tile, ms/step))."""
+    n = len(candidates) if candidates else 0
+    arr = (ljsel_batch_tile * max(n, 1))(*(candidates or []))
+    costs = np.full(max(n, 10), -1.0)
+    chosen = ljsel_batch_tile()
+    _check(lib().ljsel_batch_autotune(b, int(trial_steps), n, arr if n else None, ctypes.byref(chosen),
+                                      costs.ctypes.data))
+    return chosen, costs[:max(n, 10)].tolist()
+
+
+class Batch:
+    """Owner of one ljsel batch handle; replicas given as a list of scenario dicts."""
+
+    def __init__(self, replicas, precision=0, use_graphs=True, stream=None, device_inputs=None):
+        r0 = replicas[0]
+        self.counts = np.array([len(r["x"]) for r in replicas], np.int64)
+        self.offsets = np.concatenate([[0], np.cumsum(self.counts)])
+        self.nrep = len(replicas)
+        self.ntot = int(self.counts.sum())
+        boxes = np.stack([np.broadcast_to(np.asarray(r["box"], np.float64), (3,)) for r in replicas])
+        self.boxes = boxes
+        self.params = make_params(boxes[0], r0.get("eps", 1.0), r0.get("sigma", 1.0), r0.get("rcut", 2.5),
+                                  r0.get("mass", 1.0), r0.get("skin", 0.3), r0.get("dt", 0.005), r0.get("shift", True),
+                                  precision, use_graphs)
+        x = np.ascontiguousarray(np.concatenate([r["x"] for r in replicas]), np.float64)
+        v = np.ascontiguousarray(np.concatenate([r["v"] for r in replicas]), np.float64)
+        if device_inputs is not None:
+            x, v = device_inputs(x), device_inputs(v)
+        self.h = ljsel_batch_create(self.params, boxes, self.counts, x, v, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            ljsel_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def split(self, a):
+        return [a[self.offsets[r]:self.offsets[r + 1]] for r in range(self.nrep)]
+
+    def step(self, nsteps, eager=False):
+        (ljsel_batch_step_eager if eager else ljsel_batch_step)(self.h, nsteps)
+
+    def compute(self):
+        F = np.zeros((self.ntot, 3))
+        e, w = ljsel_batch_compute(self.h, F, self.nrep)
+        return F, e, w
+
+    def state(self):
+        x = np.zeros((self.ntot, 3))
+        v = np.zeros((self.ntot, 3))
+        ljsel_batch_get_state(self.h, x, v)
+        return x, v
+
+    def work_positions(self):
+        x = np.zeros((self.ntot, 3))
+        ljsel_batch_get_work_positions(self.h, x)
+        return x
+
+    def pairs(self):
+        _, cnt = ljsel_batch_get_pairs(self.h, 0)
+        p, cnt = ljsel_batch_get_pairs(self.h, cnt)
+        return p
+
+    def counters(self):
+        return ljsel_batch_get_counters(self.h)
+
+    def set_tile(self, **kw):
+        ljsel_batch_set_tile(self.h, make_tile(**kw))
+
+    def tile(self):
+        return ljsel_batch_get_tile(self.h).as_tuple()
+
+    def autotune(self, trial_steps=20, candidates=None):
+        return ljsel_batch_autotune(self.h, trial_steps, candidates)
