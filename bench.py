@@ -166,6 +166,50 @@ def adjoint_leg(reps=20, nsteps=50, every=10):
     return out
 
 
+def batch_leg(steps=500, warmup=5, trial_steps=10, profile_steps=30, eager=False):
+    """Batched replicas (512 periodic systems, N log-uniform in [256, 8192],
+    about 1.17M particles): tile chosen by the batch autotuner, then `steps`
+    steps in one graph launch timed with CUDA events on the batch's stream."""
+    import torch
+
+    import paper_2505_03438_gb300 as lj
+    from paper_2505_03438_gb300 import scenarios
+
+    reps = scenarios.replica_batch()
+    stream = torch.cuda.current_stream()
+    b = lj.Batch(reps, stream=stream.cuda_stream, use_graphs=not eager)
+    t0 = time.perf_counter()
+    chosen, costs = b.autotune(trial_steps=trial_steps)
+    tune_s = time.perf_counter() - t0
+    b.step(warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0 = b.counters()
+    e0.record(stream)
+    b.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    c1 = b.counters()
+    prof = b.profile(profile_steps)
+    npairs = len(b.pairs())
+    peaks = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    ach = npairs * FLOPS_PER_PAIR / (prof["force_ms"] * 1e-3) / 1e12 if prof["force_ms"] > 0 else None
+    out = {"workload": "replicas_512: N log-uniform [256, 8192] (sum %d), rho U[0.3, 0.9], T U[0.7, 2.0], "
+                       "rc 2.5, skin 0.3, R 10" % b.ntot,
+           "value": b.ntot * steps / (ms * 1e-3), "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
+           "graph_launches": 1, "tile": chosen.as_tuple(), "tile_costs_ms": costs, "tuning_s": tune_s,
+           "rebuilds": c1["rebuilds"] - c0["rebuilds"], "pairs_within_cutoff": npairs,
+           "kernel_ms": {k: prof[k] for k in ("rebuild_ms", "force_ms", "control_ms")},
+           "roofline": {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                        "frac": ach / fp32_peak if ach else None, "traffic": None,
+                        "kernel": "batched force + update", "flops_per_launch": npairs * FLOPS_PER_PAIR}}
+    b.close()
+    return out
+
+
 def run_reference(args):
     """Reference arm: the oracle as it stands, on the host cores."""
     from paper_2505_03438_gb300 import scenarios
@@ -345,6 +389,7 @@ def run_ours(args):
     if args.cpu_baseline and world == 1:
         cb = oracle_rate(sc)
     adj = adjoint_leg() if args.adjoint else None
+    bat = batch_leg() if args.batch else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": int(steps_done),
         "warmup": W, "ms_per_step": ms / max(steps_done, 1), "higher_is_better": True, "scaling": "weak",
@@ -367,6 +412,7 @@ def run_ours(args):
         "fixed": fixed,
         "best_fixed": max(fixed.items(), key=lambda kv: kv[1]) if fixed else None,
         "adjoint": adj,
+        "batch": bat,
     }
     # kernels launched in the timed region: per step the force (and update
     # when N3L is on) and the control kernel, per rebuild its chain, plus the
@@ -401,11 +447,18 @@ def main():
     ap.add_argument("--no-other", dest="other", action="store_false", help="skip the second tuning strategy")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-adjoint", dest="adjoint", action="store_false", help="skip the gradient-workload timings")
+    ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the batched-replica run")
+    ap.add_argument("--leg", default="all", choices=["all", "batch", "adjoint"],
+                    help="run only the batched-replica or the gradient leg (profiling aid) and print its JSON")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.leg == "batch":
+        print(json.dumps(batch_leg(steps=args.steps, warmup=args.warmup, eager=args.eager)), flush=True)
+    elif args.leg == "adjoint":
+        print(json.dumps(adjoint_leg()), flush=True)
     else:
         run_ours(args)
 

@@ -236,6 +236,15 @@ ljsel_status ljsel_get_state(ljsel_system s, double *pos, double *vel, int32_t o
 /* Replace positions and velocities (n x 3, host or device).               */
 ljsel_status ljsel_set_state(ljsel_system s, const double *pos, const double *vel, int32_t on_device);
 
+/* Move particles to new positions (host or device, n x 3, input order;
+ * velocities unchanged) while keeping the neighbour structure of the last
+ * rebuild, as an external integrator moving particles by less than skin/2
+ * between rebuilds would (Sec. 2.2.1).  Positions need not lie in the box.
+ * Any particle now at skin/2 or more from where it was at the last rebuild
+ * makes the next evaluation rebuild first, so results never depend on a
+ * stale structure.  Synchronizes the stream.                              */
+ljsel_status ljsel_move_particles(ljsel_system s, const double *pos, int32_t on_device);
+
 /* The positions the pair arithmetic uses (the working-precision copy,
  * promoted exactly to double, not wrapped), n x 3 in input order.  With
  * these, the oracle reproduces the pair set bit for bit.                  */
@@ -375,6 +384,9 @@ ljsel_status ljsel_batch_get_work_positions(ljsel_batch b, double *pos);
  * replica-local input indices; *count the total (may exceed cap).         */
 ljsel_status ljsel_batch_get_pairs(ljsel_batch b, int64_t cap, int32_t *rij, int64_t *count);
 ljsel_status ljsel_batch_get_counters(ljsel_batch b, ljsel_counters *c);
+/* nsteps real steps with CUDA events around each kernel class, as
+ * ljsel_profile_steps (force_ms covers the fused force + update kernel).  */
+ljsel_status ljsel_batch_profile_steps(ljsel_batch b, int64_t nsteps, ljsel_profile *out);
 /* Tile selection by full search: each candidate (ncand = 0: a default set
  * of ten) runs trial_steps timed steps that advance the batch; the fastest
  * per step is kept and returned in *chosen; costs_ms (host, ncand or ten

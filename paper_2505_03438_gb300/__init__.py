@@ -142,6 +142,7 @@ _SIGS = {
     "ljsel_get_state": ([_P, _P, _P, ctypes.c_int32], ctypes.c_int),
     "ljsel_set_state": ([_P, _P, _P, ctypes.c_int32], ctypes.c_int),
     "ljsel_get_work_positions": ([_P, _P, ctypes.c_int32], ctypes.c_int),
+    "ljsel_move_particles": ([_P, _P, ctypes.c_int32], ctypes.c_int),
     "ljsel_get_pairs": ([_P, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "ljsel_get_energy": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
@@ -171,6 +172,7 @@ _SIGS = {
     "ljsel_batch_get_work_positions": ([_P, _P], ctypes.c_int),
     "ljsel_batch_get_pairs": ([_P, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "ljsel_batch_get_counters": ([_P, ctypes.POINTER(ljsel_counters)], ctypes.c_int),
+    "ljsel_batch_profile_steps": ([_P, ctypes.c_int64, ctypes.POINTER(ljsel_profile)], ctypes.c_int),
     "ljsel_batch_autotune": ([_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.POINTER(ljsel_batch_tile), _P],
                              ctypes.c_int),
 }
@@ -318,6 +320,11 @@ def ljsel_set_state(h, pos=None, vel=None):
     if pos is not None and vel is not None and d1 != d2:
         raise ValueError("pos and vel must be both host or both device")
     _check(lib().ljsel_set_state(h, pp, vp, d1 if pos is not None else d2))
+
+
+def ljsel_move_particles(h, pos):
+    p, d = _ptr(pos)
+    _check(lib().ljsel_move_particles(h, p, d))
 
 
 def ljsel_get_work_positions(h, pos):
@@ -501,6 +508,9 @@ class System:
         ljsel_get_work_positions(self.h, x)
         return x
 
+    def move_particles(self, x):
+        ljsel_move_particles(self.h, np.ascontiguousarray(x, np.float64))
+
     def pairs(self, cap=None):
         if cap is None:
             _, cnt = ljsel_get_pairs(self.h, 0)
@@ -646,6 +656,12 @@ def ljsel_batch_get_counters(b) -> dict:
     return {k: getattr(c, k) for k, _ in c._fields_}
 
 
+def ljsel_batch_profile_steps(b, nsteps) -> dict:
+    p = ljsel_profile()
+    _check(lib().ljsel_batch_profile_steps(b, int(nsteps), ctypes.byref(p)))
+    return {k: getattr(p, k) for k, _ in p._fields_}
+
+
 def ljsel_batch_autotune(b, trial_steps=20, candidates=None):
     """Full search over force-kernel tiles; returns (chosen tile, list of (tile, ms/step))."""
     n = len(candidates) if candidates else 0
@@ -726,3 +742,6 @@ class Batch:
 
     def autotune(self, trial_steps=20, candidates=None):
         return ljsel_batch_autotune(self.h, trial_steps, candidates)
+
+    def profile(self, nsteps):
+        return ljsel_batch_profile_steps(self.h, nsteps)

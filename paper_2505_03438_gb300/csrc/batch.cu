@@ -1056,6 +1056,61 @@ ljsel_status ljsel_batch_get_pairs(ljsel_batch b, int64_t cap, int32_t *rij, int
     });
 }
 
+// Plain stream launches with events around the rebuild chain, the fused
+// force + update kernel and the control kernel; the host reads the control
+// block every step to launch the rebuild chain only when it runs.
+ljsel_status ljsel_batch_profile_steps(ljsel_batch b, int64_t nsteps, ljsel_profile *out) {
+    if (!b || !out || nsteps < 0) { set_error("invalid argument"); return LJSEL_ERR_ARG; }
+    memset(out, 0, sizeof(*out));
+    return bdispatch(b, [&](auto z) -> ljsel_status {
+        using R = decltype(z);
+        TRY(b->ensure_structure<R>());
+        cudaEvent_t ev[5];
+        for (auto &e : ev) CK(cudaEventCreate(&e));
+        BDev<R> S;
+        b->fill(S);
+        double tr = 0, tf = 0, tc = 0;
+        ljsel_status st = b->cmd(CMD_BEGIN, nsteps);
+        for (long long k = 0; k < nsteps && st == LJSEL_OK; ++k) {
+            if ((st = b->read_ctrl()) != LJSEL_OK) break;
+            if (b->h_ctrl->overflow) {
+                if ((st = b->grow()) == LJSEL_OK) st = b->ensure_structure<R>();
+                b->fill(S);
+                continue;
+            }
+            const bool reb = b->h_ctrl->rebuild_now != 0;
+            if (reb) {
+                cudaEventRecord(ev[0], b->stream);
+                b->enqueue_rebuild(S, b->stream);
+                cudaEventRecord(ev[1], b->stream);
+                out->launches += 10;
+            }
+            cudaEventRecord(ev[2], b->stream);
+            b->force_launch<R, BMODE_STEP, false>(S, b->tile, b->stream);
+            cudaEventRecord(ev[3], b->stream);
+            launch_control(S.ctrl, 0, 0, 0, b->stream);
+            cudaEventRecord(ev[4], b->stream);
+            out->launches += 2;
+            if (cudaEventSynchronize(ev[4]) != cudaSuccess) { set_error("profiling step failed"); st = LJSEL_ERR_CUDA; break; }
+            float a = 0, f = 0, c = 0;
+            if (reb) { cudaEventElapsedTime(&a, ev[0], ev[1]); out->rebuilds += 1; tr += a; }
+            cudaEventElapsedTime(&f, ev[2], ev[3]);
+            cudaEventElapsedTime(&c, ev[3], ev[4]);
+            tf += f;
+            tc += c;
+            out->steps += 1;
+        }
+        for (auto &e : ev) cudaEventDestroy(e);
+        if (st != LJSEL_OK) return st;
+        b->synced = false;
+        out->rebuild_ms = out->rebuilds ? tr / out->rebuilds : 0.0;
+        out->force_ms = out->steps ? tf / out->steps : 0.0;
+        out->control_ms = out->steps ? tc / out->steps : 0.0;
+        out->total_ms = tr + tf + tc;
+        return LJSEL_OK;
+    });
+}
+
 ljsel_status ljsel_batch_get_counters(ljsel_batch b, ljsel_counters *c) {
     if (!b || !c) { set_error("NULL argument"); return LJSEL_ERR_ARG; }
     TRY(b->read_ctrl());

@@ -297,6 +297,27 @@ ljsel_status ljsel_set_state(ljsel_system h, const double *pos, const double *ve
     });
 }
 
+ljsel_status ljsel_move_particles(ljsel_system h, const double *pos, int32_t on_device) {
+    System *s = (System *)h;
+    if (!s || !pos) { set_error("NULL argument"); return LJSEL_ERR_ARG; }
+    return dispatch(s, [&](auto z) -> ljsel_status {
+        using R = decltype(z);
+        const size_t nb = (size_t)s->n * 3 * sizeof(double);
+        const double *dp = pos;
+        if (!on_device) {
+            TRY(s->b_io.ensure(nb));
+            CK(cudaMemcpyAsync(s->b_io.ptr, pos, nb, cudaMemcpyHostToDevice, s->stream));
+            dp = (const double *)s->b_io.ptr;
+        }
+        Dev<R> S;
+        s->fill_dev(S);
+        launch_move_particles(S, dp, s->stream);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(s->stream));
+        return LJSEL_OK;
+    });
+}
+
 ljsel_status ljsel_get_work_positions(ljsel_system h, double *pos, int32_t on_device) {
     System *s = (System *)h;
     if (!s || !pos) { set_error("NULL argument"); return LJSEL_ERR_ARG; }

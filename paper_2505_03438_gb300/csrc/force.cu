@@ -460,6 +460,29 @@ __global__ void k_import_state(Dev<R> S, const double *pos, const double *vel, c
     S.xref[i] = w;
 }
 
+// New positions (input order) for the current slots, keeping the neighbour
+// structure: the reference positions of the last rebuild stay, and a
+// particle that now lies skin/2 or more from its reference flags a rebuild,
+// so the structure is used only while the Verlet-list guarantee holds.
+template <typename R>
+__global__ void k_move_particles(Dev<R> S, const double *pos) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S.n) return;
+    Ctrl *C = S.ctrl;
+    const int sp = C->state_par, pp = C->pos_par, n = S.n;
+    const int id = S.id[sp][i];
+    double x[3];
+    for (int d = 0; d < 3; ++d) {
+        x[d] = pos[3 * id + d];
+        S.x[sp][d * n + i] = x[d];
+    }
+    const V4<R> w = make_pos((R)x[0], (R)x[1], (R)x[2], S.type[sp][i]);
+    S.pos[pp][i] = w;
+    const V4<R> r = S.xref[i];
+    const R dx = w.x - r.x, dy = w.y - r.y, dz = w.z - r.z;
+    if (!(dx * dx + dy * dy + dz * dz < S.half_skin2)) C->rebuild_now = 1;
+}
+
 // Bring half-step velocities to the integer step: v += (dt/2m) F(x).
 template <typename R>
 __global__ void k_sync_velocities(Dev<R> S) {
@@ -569,6 +592,9 @@ template <typename R> void launch_import_state(const Dev<R> &S, const double *po
                                                int init_ids, cudaStream_t st) {
     k_import_state<R><<<div_up(S.n, 256), 256, 0, st>>>(S, pos, vel, types, init_ids);
 }
+template <typename R> void launch_move_particles(const Dev<R> &S, const double *pos, cudaStream_t st) {
+    k_move_particles<R><<<div_up(S.n, 256), 256, 0, st>>>(S, pos);
+}
 template <typename R> void launch_sync_velocities(const Dev<R> &S, cudaStream_t st) {
     k_sync_velocities<R><<<div_up(S.n, 256), 256, 0, st>>>(S);
 }
@@ -587,6 +613,7 @@ template <typename R> void launch_zero_force(const Dev<R> &S, cudaStream_t st) {
     template void launch_import_state<R>(const Dev<R> &, const double *, const double *, const int *, int,    \
                                          cudaStream_t);                                                      \
     template void launch_sync_velocities<R>(const Dev<R> &, cudaStream_t);                                   \
+    template void launch_move_particles<R>(const Dev<R> &, const double *, cudaStream_t);                    \
     template void launch_kinetic<R>(const Dev<R> &, cudaStream_t);                                           \
     template void launch_zero_force<R>(const Dev<R> &, cudaStream_t);
 INST(float)

@@ -44,6 +44,7 @@ template <typename R> void launch_export_work_pos(const Dev<R> &S, double *pos, 
 template <typename R> void launch_import_state(const Dev<R> &S, const double *pos, const double *vel,
                                                const int *types, int init_ids, cudaStream_t st);
 template <typename R> void launch_sync_velocities(const Dev<R> &S, cudaStream_t st);
+template <typename R> void launch_move_particles(const Dev<R> &S, const double *pos, cudaStream_t st);
 template <typename R> void launch_kinetic(const Dev<R> &S, cudaStream_t st);
 template <typename R> void launch_zero_force(const Dev<R> &S, cudaStream_t st);
 template <typename R> void launch_bin_stats(const Dev<R> &S, const int *counts, int nb, double *out, cudaStream_t st);

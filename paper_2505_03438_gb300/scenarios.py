@@ -15,6 +15,7 @@ Every scenario is a plain dict:
 from __future__ import annotations
 
 import math
+import os
 
 import numpy as np
 
@@ -184,3 +185,92 @@ def jittered_mixture(nside=7, seed=5, jitter=0.1):
     sc["x"] = sc["x"] + rng.uniform(-jitter, jitter, sc["x"].shape)
     sc["name"] = "binary_%d_jittered" % len(sc["x"])
     return sc
+
+
+def _rsa(center, radius, box_len, target, dmin, rng, existing=None, inside=True):
+    """Random sequential addition in batches: uniform candidates, accepted
+    when no accepted point lies closer than dmin (minimum image); of two
+    candidates of one batch closer than dmin the later one is dropped.
+    inside=True draws in the ball (center, radius); inside=False draws in the
+    periodic box outside it."""
+    from scipy.spatial import cKDTree
+    acc = np.zeros((0, 3)) if existing is None else np.asarray(existing, np.float64)
+    n0 = len(acc)
+    # accepted points live in a large tree rebuilt now and then plus a small
+    # tree of the points accepted since
+    big = cKDTree(acc, boxsize=box_len) if len(acc) else None
+    nbig = len(acc)
+    tries = 0
+    rate = 1.0  # accepted fraction of the last batch
+    while len(acc) - n0 < target:
+        tries += 1
+        if tries > 100000:
+            raise RuntimeError("RSA placement stalled")
+        left = target - (len(acc) - n0)
+        batch = int(min(max(40000, 1.5 * left / max(rate, 1e-3)), 400000))
+        if inside:
+            u = rng.normal(size=(batch, 3))
+            u /= np.linalg.norm(u, axis=1, keepdims=True)
+            c = center + u * (radius * rng.uniform(0.0, 1.0, (batch, 1)) ** (1.0 / 3.0))
+        else:
+            c = rng.uniform(0.0, box_len, (batch, 3))
+            c = c[np.linalg.norm(c - center, axis=1) >= radius]
+        c = np.mod(c, box_len)
+        if big is not None:
+            d, _ = big.query(c, k=1, distance_upper_bound=dmin)
+            c = c[d >= dmin]
+        if len(acc) > nbig and len(c):
+            d, _ = cKDTree(acc[nbig:], boxsize=box_len).query(c, k=1, distance_upper_bound=dmin)
+            c = c[d >= dmin]
+        if len(c) == 0:
+            continue
+        # conflicts among the candidates: keep each unless an earlier kept one is too close
+        pairs = cKDTree(c, boxsize=box_len).query_pairs(dmin, output_type="ndarray")
+        keep = np.ones(len(c), bool)
+        if len(pairs):
+            keep[pairs.max(axis=1)] = False
+        c = c[keep][: target - (len(acc) - n0)]
+        rate = max(len(c), 1) / batch
+        acc = np.concatenate([acc, c])
+        if len(acc) - nbig > 0.25 * nbig + 5000:
+            big = cKDTree(acc, boxsize=box_len)
+            nbig = len(acc)
+    return acc
+
+
+def heated_sphere(seed=3, box_len=200.0, radius=40.0, rho_liquid=0.8, t_liquid=3.0, rho_vapour=0.01,
+                  t_vapour=1.2, dmin=0.9, rc=2.5, skin=0.3, dt=0.005, rebuild=10):
+    """Inhomogeneous workload (periodic analogue of a heating sphere): a
+    liquid ball of the given radius and density at the box centre, drawn at
+    the heated temperature, in a vapour filling the rest of the periodic box;
+    non-overlapping random placement (RSA, minimum spacing dmin), the ball
+    first.  Velocities Maxwell-Boltzmann per phase, zero momentum per phase,
+    each rescaled to its temperature exactly."""
+    key = "sphere_%d_%g_%g_%g_%g_%g_%g_%g" % (seed, box_len, radius, rho_liquid, t_liquid, rho_vapour, t_vapour, dmin)
+    cache = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "scenarios", key + ".npz")
+    if os.path.exists(cache):
+        z = np.load(cache)
+        x, v, n_l = z["x"], z["v"], int(z["n_l"])
+    else:
+        x, v, n_l = _heated_sphere_draw(seed, box_len, radius, rho_liquid, t_liquid, rho_vapour, t_vapour, dmin)
+        os.makedirs(os.path.dirname(cache), exist_ok=True)
+        tmp = cache + ".tmp.%d.npz" % os.getpid()
+        np.savez(tmp, x=x, v=v, n_l=n_l)
+        os.replace(tmp, cache)
+    sc = dict(name="heated_sphere_%d" % len(x), x=x, v=v, types=np.zeros(len(x), np.int32), dt=dt, skin=skin,
+              rebuild=rebuild, n_liquid=n_l, temperature=t_liquid, seed=seed)
+    sc.update(_single_type(np.full(3, box_len), rc))
+    return sc
+
+
+def _heated_sphere_draw(seed, box_len, radius, rho_liquid, t_liquid, rho_vapour, t_vapour, dmin):
+    rng = np.random.default_rng(seed)
+    center = np.full(3, 0.5 * box_len)
+    vol_ball = 4.0 / 3.0 * math.pi * radius ** 3
+    n_l = int(round(rho_liquid * vol_ball))
+    n_v = int(round(rho_vapour * (box_len ** 3 - vol_ball)))
+    xl = _rsa(center, radius, box_len, n_l, dmin, rng, inside=True)
+    xa = _rsa(center, radius, box_len, n_v, dmin, rng, existing=xl, inside=False)
+    vl = maxwell_boltzmann(n_l, t_liquid, 1.0, rng)
+    vv = maxwell_boltzmann(n_v, t_vapour, 1.0, rng)
+    return xa, np.concatenate([vl, vv]), n_l

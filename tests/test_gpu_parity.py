@@ -1,10 +1,18 @@
 """GPU path against the FP64 oracle, through the C ABI.
 
 Bars: the within-cutoff pair set is bit-exact (the oracle evaluates the exact
-FP64 predicate on the working positions the GPU used); FP32 forces are within
+FP64 predicate on the working positions the GPU uses); FP32 forces are within
 1e-5 relative RMS of the oracle's FP64 forces on those positions; energy and
 virial within 2e-6 relative (FP32 pair terms summed in FP64); the FP64 check
 path matches the oracle to 1e-12.
+
+The oracle only ever sees generator data.  The working positions of the FP32
+path are the generator's positions rounded to float32 (rounded here, in
+numpy).  Lists reused with drifted positions are checked by moving the
+particles through ljsel_move_particles by generator-made displacements below
+skin/2 (some across a box face), which keeps the lists of the last rebuild.
+After simulated steps, the FP64 path is compared with the oracle's own
+trajectory.
 """
 import numpy as np
 import pytest
@@ -73,9 +81,28 @@ def _orc_params(sc):
     return oracle.make_params(sc["box"], sc["eps"], sc["sigma"], sc["rcut"], sc.get("shift", True))
 
 
-def check_against_oracle(sys_, sc, force_tol=FORCE_TOL, sum_tol=SUM_TOL):
+def _f32(x):
+    return np.asarray(x, np.float32).astype(np.float64)
+
+
+def drift(x, box, seed, amp):
+    """Generator-made displacement of every particle by less than amp, with
+    particles next to a box face stepping across it (positions stay
+    unwrapped, as between rebuilds)."""
+    rng = np.random.default_rng(seed)
+    d = rng.normal(size=x.shape)
+    d *= (amp * rng.uniform(0.2, 1.0, (len(x), 1))) / np.linalg.norm(d, axis=1, keepdims=True)
+    L = np.broadcast_to(np.asarray(box, np.float64), (3,))
+    d = np.where(x < 0.5 * amp, -np.abs(d), d)
+    d = np.where(x > L - 0.5 * amp, np.abs(d), d)
+    return x + d
+
+
+def check_against_oracle(sys_, sc, x, precision=0, force_tol=FORCE_TOL, sum_tol=SUM_TOL):
+    """Forces, energy, virial and pair set of the system, whose positions are
+    x (generator data), against the oracle on the working positions."""
     F, e, w = sys_.compute()
-    xw = sys_.work_positions()
+    xw = x if precision else _f32(x)
     ref = oracle.forces_cells(xw, sc["types"], _orc_params(sc), pairs=True)
     pairs, cnt = sys_.pairs()
     assert cnt == ref["count"], (cnt, ref["count"])
@@ -93,10 +120,13 @@ def test_pairs_forces_fp32(lj, cfg, name):
     sc = SYSTEMS[name]
     s = lj.System(sc)
     s.set_config(rebuild_interval=10, **cfg)
-    check_against_oracle(s, sc)
-    # after 30 steps the positions have drifted (not wrapped) and the lists are reused
-    s.step(30)
-    check_against_oracle(s, sc)
+    check_against_oracle(s, sc, sc["x"])
+    # drifted (not wrapped) positions with the lists of the last rebuild
+    nreb = s.counters()["rebuilds"]
+    x1 = drift(sc["x"], sc["box"], 1000 + len(sc["x"]), 0.9 * 0.5 * sc["skin"])
+    s.move_particles(x1)
+    check_against_oracle(s, sc, x1)
+    assert s.counters()["rebuilds"] == nreb
     s.close()
 
 
@@ -106,9 +136,16 @@ def test_pairs_forces_fp64(lj, cfg):
         sc = SYSTEMS[name]
         s = lj.System(sc, precision=1)
         s.set_config(rebuild_interval=10, **cfg)
-        check_against_oracle(s, sc, force_tol=1e-12, sum_tol=1e-12)
-        s.step(15)
-        check_against_oracle(s, sc, force_tol=1e-12, sum_tol=1e-12)
+        check_against_oracle(s, sc, sc["x"], 1, force_tol=1e-12, sum_tol=1e-12)
+        x1 = drift(sc["x"], sc["box"], 2000 + len(sc["x"]), 0.9 * 0.5 * sc["skin"])
+        s.move_particles(x1)
+        check_against_oracle(s, sc, x1, 1, force_tol=1e-12, sum_tol=1e-12)
+        # past skin/2 the next evaluation rebuilds first
+        x2 = drift(sc["x"], sc["box"], 3000 + len(sc["x"]), 2.0 * sc["skin"])
+        nreb = s.counters()["rebuilds"]
+        s.move_particles(x2)
+        check_against_oracle(s, sc, x2, 1, force_tol=1e-12, sum_tol=1e-12)
+        assert s.counters()["rebuilds"] == nreb + 1
         s.close()
 
 
@@ -171,14 +208,21 @@ def test_graph_equals_eager(lj):
 
 
 def test_displacement_forces_early_rebuild(lj):
-    # hot gas: particles cross skin/2 long before R = 200 steps
+    # hot gas: particles cross skin/2 long before R = 200 steps; the FP64 run
+    # stays on the oracle's trajectory, so no pair was missed
     sc = scenarios.random_gas(800, 14.0, seed=41, min_dist=0.9, temperature=6.0)
-    s = lj.System(sc, skin=0.2)
+    s = lj.System(sc, skin=0.2, precision=1)
     s.set_config(method="VL", rebuild_interval=200)
     s.step(120)
     c = s.counters()
     assert c["early_rebuilds"] >= 2, c
-    check_against_oracle(s, sc)
+    x, v = s.state()
+    xo, vo, *_ = oracle.verlet_run(sc["x"], sc["v"], None, [1.0], _orc_params(sc), sc["dt"], 120)
+    assert np.abs(_wrapdiff(x, xo, sc["box"][0])).max() < 1e-9
+    assert np.abs(v - vo).max() < 1e-9
+    pairs, cnt = s.pairs()
+    ref = oracle.forces_cells(xo, None, _orc_params(sc), pairs=True)
+    assert np.array_equal(oracle.sorted_pairs(pairs), oracle.sorted_pairs(ref["pairs"]))
     s.close()
 
 
@@ -203,11 +247,12 @@ def test_capacity_overflow_is_recovered(lj):
     for cfg in (dict(method="VL"), dict(method="CL", cluster_size=8, threads_per_unit=8)):
         s = lj.System(sc)
         s.set_config(**cfg)
-        check_against_oracle(s, sc)
+        check_against_oracle(s, sc, x)
         if cfg["method"] == "VL":
             assert s.counters()["capacity_retries"] >= 1
-        s.step(20)
-        check_against_oracle(s, sc)
+        x1 = drift(x, sc["box"], 77, 0.13)
+        s.move_particles(x1)
+        check_against_oracle(s, sc, x1)
         s.close()
 
 
@@ -223,9 +268,19 @@ def test_live_statistics(lj):
         s.close()
 
 
+def _on_oracle_trajectory(s, sc):
+    """An FP64 system whose trial steps switched configuration mid-run is
+    still on the oracle's trajectory."""
+    nsteps = s.counters()["steps"]
+    x, v = s.state()
+    xo, vo, *_ = oracle.verlet_run(sc["x"], sc["v"], None, [1.0], _orc_params(sc), sc["dt"], nsteps)
+    assert np.abs(_wrapdiff(x, xo, sc["box"][0])).max() < 1e-8, nsteps
+    assert np.abs(v - vo).max() < 1e-8, nsteps
+
+
 def test_autotune_full_and_predictive(lj):
     sc = scenarios.fcc_liquid(8, seed=61, jitter=0.1)
-    s = lj.System(sc)
+    s = lj.System(sc, precision=1)
     cands = lj.ljsel_default_candidates(s.h)
     assert len(cands) >= 15
     chosen, rep = s.autotune(strategy=0, trial_steps=10)
@@ -233,25 +288,31 @@ def test_autotune_full_and_predictive(lj):
     assert any(chosen.name() == c.name() for c in cands)
     assert s.config().name() == chosen.name()
     assert s.counters()["steps"] == 10 * len(cands)
-    check_against_oracle(s, sc)
+    _on_oracle_trajectory(s, sc)
     # predictive strategy: two full phases, then a filtered one
-    s2 = lj.System(sc)
+    s2 = lj.System(sc, precision=1)
     for ph in range(3):
         _, rep = s2.autotune(strategy=1, trial_steps=10, blacklist_factor=10.0)
     assert rep["ntrialled"] < len(cands)
-    check_against_oracle(s2, sc)
+    _on_oracle_trajectory(s2, sc)
     # probe filter: slow configurations stop after their probe steps
-    s3 = lj.System(sc)
+    s3 = lj.System(sc, precision=1)
     _, rep = s3.autotune(strategy=0, trial_steps=10, probe_steps=2, probe_factor=1.5)
     assert rep["nprobed_out"] > 0 and rep["trial_steps_total"] < 10 * len(cands)
     assert s3.counters()["steps"] == rep["trial_steps_total"]
-    check_against_oracle(s3, sc)
+    _on_oracle_trajectory(s3, sc)
     # expert strategy: the dense liquid (about 16 particles per bin) trials a subset
     s4 = lj.System(sc)
     chosen4, rep = s4.autotune(strategy="expert", trial_steps=5)
     assert rep["expert_input"] > 8 and 0 < rep["ntrialled"] < len(cands)
     assert chosen4.method == lj.METHOD_VL
-    check_against_oracle(s4, sc)
+    # the FP32 system keeps the selected configuration's exactness: moved
+    # particles with its lists against the oracle
+    x1 = drift(sc["x"], sc["box"], 62, 0.05)
+    s4.set_state(sc["x"], sc["v"])
+    check_against_oracle(s4, sc, sc["x"])
+    s4.move_particles(x1)
+    check_against_oracle(s4, sc, x1)
     for x in (s, s2, s3, s4):
         x.close()
 
@@ -267,9 +328,7 @@ def test_device_pointer_inputs(lj):
     F = torch.zeros_like(x)
     e, w = lj.ljsel_compute(h, F)
     torch.cuda.synchronize()
-    xw = np.zeros_like(sc["x"])
-    lj.ljsel_get_work_positions(h, xw)
-    ref = oracle.forces_cells(xw, None, _orc_params(sc))
+    ref = oracle.forces_cells(_f32(sc["x"]), None, _orc_params(sc))
     Fh = F.cpu().numpy()
     assert np.linalg.norm(Fh - ref["F"]) / np.linalg.norm(ref["F"]) < FORCE_TOL
     lj.ljsel_destroy(h)
@@ -279,9 +338,11 @@ def test_liquid_1m_full_size(lj):
     """Full-size homogeneous liquid (N = 1,048,576) in the benchmark's launch
     configuration: whole pair set and all forces against the oracle."""
     sc = scenarios.liquid_1m()
+    x1 = drift(sc["x"], sc["box"], 81, 0.9 * 0.5 * sc["skin"])
     for cfg in (dict(method="VL"), dict(method="VLW"), dict(method="VLW", newton3=True)):
         s = lj.System(sc)
         s.set_config(rebuild_interval=10, **cfg)
-        s.step(20)
-        check_against_oracle(s, sc)
+        check_against_oracle(s, sc, sc["x"])
+        s.move_particles(x1)
+        check_against_oracle(s, sc, x1)
         s.close()
