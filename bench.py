@@ -210,6 +210,65 @@ def batch_leg(steps=500, warmup=5, trial_steps=10, profile_steps=30, eager=False
     return out
 
 
+def inhomogeneous_leg(steps=20000, every=1000, strategy="predictive", fixed_steps=None):
+    """Heated liquid ball (radius 40, density 0.8, T 3.0) in vapour (density
+    0.01, T 1.2), periodic box 200, about 292k particles: `steps` steps with
+    a tuning phase every `every` steps (trial steps count as steps), against
+    every fixed configuration run over the same steps from the same state."""
+    import torch
+
+    import paper_2505_03438_gb300 as lj
+    from paper_2505_03438_gb300 import scenarios
+
+    sc = scenarios.heated_sphere()
+    n = len(sc["x"])
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    s = lj.System(sc, stream=stream.cuda_stream)
+    s.step(3)
+    phases = []
+
+    def tuned_run():
+        for k in range(steps // every):
+            c, rep = s.autotune(strategy=strategy, trial_steps=10, probe_steps=2, probe_factor=2.0)
+            s.step(every - rep["trial_steps_total"])
+            phases.append({"step": k * every, "chosen": c.name(), "ntrialled": rep["ntrialled"],
+                           "phase_ms": rep["phase_ms"], "overhead_ms": rep["overhead_ms"]})
+
+    ms = timed(tuned_run)
+    s.close()
+    fixed = {}
+    fs = steps if fixed_steps is None else fixed_steps
+    probe = lj.System(sc)
+    cands = lj.ljsel_default_candidates(probe.h)
+    probe.close()
+    for c in cands:
+        f = lj.System(sc, stream=stream.cuda_stream)
+        try:
+            lj.ljsel_set_config(f.h, c)
+            f.step(3)
+            fixed[c.name()] = n * fs / (timed(lambda: f.step(fs)) * 1e-3)
+        except lj.LjselError:
+            pass
+        f.close()
+    best = max(fixed.items(), key=lambda kv: kv[1]) if fixed else None
+    return {"workload": "heated_sphere: N=%d, box 200, ball r 40 rho 0.8 T 3.0, vapour rho 0.01 T 1.2, rc 2.5, "
+                        "skin 0.3" % n,
+            "value": n * steps / (ms * 1e-3), "unit": UNIT, "steps": steps, "retune_every": every,
+            "strategy": strategy, "tuning_overhead_ms": sum(p["overhead_ms"] for p in phases),
+            "tuning_phase_ms": sum(p["phase_ms"] for p in phases), "phases": phases,
+            "fixed_steps": fs, "fixed": fixed, "best_fixed": best}
+
+
 def run_reference(args):
     """Reference arm: the oracle as it stands, on the host cores."""
     from paper_2505_03438_gb300 import scenarios
@@ -390,6 +449,7 @@ def run_ours(args):
         cb = oracle_rate(sc)
     adj = adjoint_leg() if args.adjoint else None
     bat = batch_leg() if args.batch else None
+    inh = inhomogeneous_leg(fixed_steps=args.inhomo_fixed_steps) if args.inhomo else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": int(steps_done),
         "warmup": W, "ms_per_step": ms / max(steps_done, 1), "higher_is_better": True, "scaling": "weak",
@@ -413,6 +473,7 @@ def run_ours(args):
         "best_fixed": max(fixed.items(), key=lambda kv: kv[1]) if fixed else None,
         "adjoint": adj,
         "batch": bat,
+        "inhomogeneous": inh,
     }
     # kernels launched in the timed region: per step the force (and update
     # when N3L is on) and the control kernel, per rebuild its chain, plus the
@@ -448,7 +509,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-adjoint", dest="adjoint", action="store_false", help="skip the gradient-workload timings")
     ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the batched-replica run")
-    ap.add_argument("--leg", default="all", choices=["all", "batch", "adjoint"],
+    ap.add_argument("--no-inhomo", dest="inhomo", action="store_false", help="skip the heated-sphere re-tuning run")
+    ap.add_argument("--inhomo-fixed-steps", type=int, default=None,
+                    help="steps per fixed configuration in the heated-sphere comparison (default: all 20000)")
+    ap.add_argument("--leg", default="all", choices=["all", "batch", "adjoint", "inhomo"],
                     help="run only the batched-replica or the gradient leg (profiling aid) and print its JSON")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -459,6 +523,8 @@ def main():
         print(json.dumps(batch_leg(steps=args.steps, warmup=args.warmup, eager=args.eager)), flush=True)
     elif args.leg == "adjoint":
         print(json.dumps(adjoint_leg()), flush=True)
+    elif args.leg == "inhomo":
+        print(json.dumps(inhomogeneous_leg(fixed_steps=args.inhomo_fixed_steps)), flush=True)
     else:
         run_ours(args)
 

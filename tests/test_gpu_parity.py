@@ -98,16 +98,18 @@ def drift(x, box, seed, amp):
     return x + d
 
 
-def check_against_oracle(sys_, sc, x, precision=0, force_tol=FORCE_TOL, sum_tol=SUM_TOL):
+def check_against_oracle(sys_, sc, x, precision=0, force_tol=FORCE_TOL, sum_tol=SUM_TOL, forces=True):
     """Forces, energy, virial and pair set of the system, whose positions are
-    x (generator data), against the oracle on the working positions."""
+    x (generator data), against the oracle on the working positions.  On a
+    perfect lattice every force cancels to rounding, so there the relative
+    force error is not defined and forces=False skips it."""
     F, e, w = sys_.compute()
     xw = x if precision else _f32(x)
     ref = oracle.forces_cells(xw, sc["types"], _orc_params(sc), pairs=True)
     pairs, cnt = sys_.pairs()
     assert cnt == ref["count"], (cnt, ref["count"])
     assert np.array_equal(oracle.sorted_pairs(pairs), oracle.sorted_pairs(ref["pairs"]))
-    rel = np.linalg.norm(F - ref["F"]) / np.linalg.norm(ref["F"])
+    rel = np.linalg.norm(F - ref["F"]) / np.linalg.norm(ref["F"]) if forces else 0.0
     assert rel <= force_tol, rel
     assert abs(e - ref["U"]) <= sum_tol * max(abs(ref["U"]), 1.0), (e, ref["U"])
     assert abs(w - ref["W"]) <= sum_tol * max(abs(ref["W"]), 1.0), (w, ref["W"])
@@ -342,7 +344,7 @@ def test_liquid_1m_full_size(lj):
     for cfg in (dict(method="VL"), dict(method="VLW"), dict(method="VLW", newton3=True)):
         s = lj.System(sc)
         s.set_config(rebuild_interval=10, **cfg)
-        check_against_oracle(s, sc, sc["x"])
+        check_against_oracle(s, sc, sc["x"], forces=False)  # perfect fcc lattice: all forces vanish
         s.move_particles(x1)
         check_against_oracle(s, sc, x1)
         s.close()
