@@ -210,11 +210,13 @@ def batch_leg(steps=500, warmup=5, trial_steps=10, profile_steps=30, eager=False
     return out
 
 
-def inhomogeneous_leg(steps=20000, every=1000, strategy="predictive", fixed_steps=None):
+def inhomogeneous_leg(steps=20000, every=1000, strategy="predictive", fixed_steps=None, skip_within=0.05):
     """Heated liquid ball (radius 40, density 0.8, T 3.0) in vapour (density
     0.01, T 1.2), periodic box 200, about 292k particles: `steps` steps with
-    a tuning phase every `every` steps (trial steps count as steps), against
-    every fixed configuration run over the same steps from the same state."""
+    a tuning phase every `every` steps (trial steps count as steps; a phase
+    whose live statistics moved less than skip_within since the last phase
+    with trials is skipped), against every fixed configuration run over the
+    same steps from the same state."""
     import torch
 
     import paper_2505_03438_gb300 as lj
@@ -239,10 +241,11 @@ def inhomogeneous_leg(steps=20000, every=1000, strategy="predictive", fixed_step
 
     def tuned_run():
         for k in range(steps // every):
-            c, rep = s.autotune(strategy=strategy, trial_steps=10, probe_steps=2, probe_factor=2.0)
+            c, rep = s.autotune(strategy=strategy, trial_steps=10, probe_steps=2, probe_factor=2.0,
+                                skip_within=skip_within)
             s.step(every - rep["trial_steps_total"])
             phases.append({"step": k * every, "chosen": c.name(), "ntrialled": rep["ntrialled"],
-                           "phase_ms": rep["phase_ms"], "overhead_ms": rep["overhead_ms"]})
+                           "skipped": rep["skipped"], "phase_ms": rep["phase_ms"], "overhead_ms": rep["overhead_ms"]})
 
     ms = timed(tuned_run)
     s.close()
@@ -264,7 +267,9 @@ def inhomogeneous_leg(steps=20000, every=1000, strategy="predictive", fixed_step
     return {"workload": "heated_sphere: N=%d, box 200, ball r 40 rho 0.8 T 3.0, vapour rho 0.01 T 1.2, rc 2.5, "
                         "skin 0.3" % n,
             "value": n * steps / (ms * 1e-3), "unit": UNIT, "steps": steps, "retune_every": every,
-            "strategy": strategy, "tuning_overhead_ms": sum(p["overhead_ms"] for p in phases),
+            "strategy": strategy, "skip_within": skip_within,
+            "phases_skipped": sum(p["skipped"] for p in phases),
+            "tuning_overhead_ms": sum(p["overhead_ms"] for p in phases),
             "tuning_phase_ms": sum(p["phase_ms"] for p in phases), "phases": phases,
             "fixed_steps": fs, "fixed": fixed, "best_fixed": best}
 

@@ -149,6 +149,12 @@ typedef struct ljsel_tuner_opts {
                                   (0: always run trial_steps)                 */
     int32_t reserved;
     double probe_factor;       /* e.g. 2.0                                     */
+    double skip_within;        /* > 0: when the live statistics (mean,
+                                  relative std and max particles per CSF-1
+                                  bin, Sec. 4) all differ by less than this
+                                  relative amount from those at the last phase
+                                  that ran trials, the phase is skipped and the
+                                  configuration kept (0: never skip)          */
 } ljsel_tuner_opts;
 
 /* Result of the last tuning phase.                                        */
@@ -162,7 +168,7 @@ typedef struct ljsel_tuner_report {
     double overhead_ms;        /* sum over trials of (trial - chosen) cost    */
     int64_t trial_steps_total; /* steps advanced by trials in the last phase  */
     int32_t nprobed_out;       /* trials stopped after their probe            */
-    int32_t reserved;
+    int32_t skipped;           /* 1: the phase was skipped (skip_within)      */
     double expert_input;       /* expert: mean particles per CSF-1 bin        */
 } ljsel_tuner_report;
 

@@ -93,6 +93,7 @@ class ljsel_tuner_opts(ctypes.Structure):
         ("probe_steps", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
         ("probe_factor", ctypes.c_double),
+        ("skip_within", ctypes.c_double),
     ]
 
 
@@ -107,7 +108,7 @@ class ljsel_tuner_report(ctypes.Structure):
         ("overhead_ms", ctypes.c_double),
         ("trial_steps_total", ctypes.c_int64),
         ("nprobed_out", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("skipped", ctypes.c_int32),
         ("expert_input", ctypes.c_double),
     ]
 
@@ -386,8 +387,9 @@ def ljsel_default_candidates(h):
 
 
 def ljsel_autotune(h, strategy=0, trial_steps=10, predict_factor=2.0, blacklist_factor=10.0, retrial_phases=4,
-                   candidates=None, probe_steps=0, probe_factor=2.0):
+                   candidates=None, probe_steps=0, probe_factor=2.0, skip_within=0.0):
     o = ljsel_tuner_opts()
+    o.skip_within = float(skip_within)
     o.strategy = {"full": 0, "predictive": 1, "expert": 2}.get(strategy, strategy)
     o.probe_steps = int(probe_steps)
     o.probe_factor = float(probe_factor)

@@ -554,6 +554,29 @@ ljsel_status ljsel_autotune(ljsel_system h, const ljsel_tuner_opts *opts, ljsel_
         return LJSEL_ERR_ARG;
     }
     auto t0 = std::chrono::steady_clock::now();
+    if (!(opts->skip_within >= 0)) { set_error("skip_within must be >= 0"); return LJSEL_ERR_ARG; }
+    // live statistics: the expert input, and the test for skipping a phase
+    ljsel_stats st_now{};
+    const bool need_stats = opts->strategy == 2 || opts->skip_within > 0;
+    if (need_stats) TRY(ljsel_get_stats(h, &st_now));
+    if (opts->skip_within > 0 && s->have_tuned_stats) {
+        auto close = [&](double a, double b) { return std::fabs(a - b) <= opts->skip_within * std::max(std::fabs(b), 1e-12); };
+        const ljsel_stats &o = s->tuned_stats;
+        if (close(st_now.mean, o.mean) && close(st_now.rel_std, o.rel_std) && close(st_now.max, o.max)) {
+            ljsel_tuner_report r = s->last_report;
+            r.phase = s->tuner_phase;
+            r.ntrialled = 0;
+            r.nprobed_out = 0;
+            r.overhead_ms = 0;
+            r.trial_steps_total = 0;
+            r.skipped = 1;
+            r.phase_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            s->last_report = r;
+            if (chosen) *chosen = s->cfg;
+            if (report) *report = r;
+            return LJSEL_OK;
+        }
+    }
     std::vector<ljsel_config> cands;
     if (opts->ncandidates > 0) {
         if (!opts->candidates) { set_error("candidates is NULL"); return LJSEL_ERR_ARG; }
@@ -578,8 +601,7 @@ ljsel_status ljsel_autotune(ljsel_system h, const ljsel_tuner_opts *opts, ljsel_
     std::vector<char> trial(cands.size(), 1);
     double expert_x = -1.0;
     if (opts->strategy == 2) {
-        ljsel_stats st;
-        TRY(ljsel_get_stats(h, &st));
+        const ljsel_stats &st = st_now;
         expert_x = st.mean;
         int any = 0;
         for (size_t k = 0; k < cands.size(); ++k) {
@@ -699,6 +721,10 @@ ljsel_status ljsel_autotune(ljsel_system h, const ljsel_tuner_opts *opts, ljsel_
     for (auto *e : ent) nbl += e->blacklisted;
     TRY(ljsel_set_config(h, &cands[best_k]));
     s->tuner_phase += 1;
+    if (need_stats) {
+        s->tuned_stats = st_now;
+        s->have_tuned_stats = true;
+    }
     auto t1 = std::chrono::steady_clock::now();
     ljsel_tuner_report r{};
     r.phase = s->tuner_phase;

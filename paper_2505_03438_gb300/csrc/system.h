@@ -84,6 +84,8 @@ struct System {
     std::vector<TunerEntry> tuner;
     int tuner_phase = 0;
     ljsel_tuner_report last_report{};
+    bool have_tuned_stats = false;
+    ljsel_stats tuned_stats{};  // live statistics at the last phase that ran trials
 
     ~System();
     std::vector<Buf *> all_bufs();

@@ -73,3 +73,18 @@ def test_retuning_phases_stay_on_the_oracle_trajectory(strategy):
     xo, vo, *_ = oracle.verlet_run(sc["x"], sc["v"], None, [1.0], _op(sc), sc["dt"], nsteps)
     assert np.abs(_wrapdiff(x, xo, sc["box"][0])).max() < 1e-8, chosen
     assert np.abs(v - vo).max() < 1e-8, chosen
+
+
+def test_phase_skipped_while_statistics_hold():
+    """With skip_within > 0 a phase whose live statistics match those of the
+    last phase that ran trials keeps the configuration and runs no trial."""
+    sc = scenarios.heated_sphere(box_len=60.0, radius=15.0, seed=31)
+    s = lj.System(sc)
+    c1, r1 = s.autotune(strategy="predictive", trial_steps=2, skip_within=0.05)
+    assert r1["skipped"] == 0 and r1["ntrialled"] > 0
+    steps = s.counters()["steps"]
+    c2, r2 = s.autotune(strategy="predictive", trial_steps=2, skip_within=0.05)
+    assert r2["skipped"] == 1 and r2["ntrialled"] == 0 and r2["phase"] == r1["phase"]
+    assert c2.name() == c1.name() and s.counters()["steps"] == steps
+    c3, r3 = s.autotune(strategy="predictive", trial_steps=2, skip_within=0.0)
+    assert r3["skipped"] == 0 and r3["phase"] == r1["phase"] + 1
