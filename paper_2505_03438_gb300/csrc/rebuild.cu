@@ -224,13 +224,15 @@ __global__ void k_sortgather(Dev<R> S) {
     }
 }
 
-// Verlet-list rows of the particles of one cell (one warp per cell, lane =
-// particle, 32 at a time): all j in the 27 stencil cells with r^2 < r_list^2
-// (working precision), j != i; with N3L only j > i.  For each of the 9
-// neighbouring (y, z) rows the three stencil cells cx-1, cx, cx+1 are one
-// run of consecutive sorted particles (split only at a periodic x edge), so
-// the whole warp walks 9 runs in lockstep with uniform-address loads, four
-// candidates at a time.  Entries without an image go to the front of the
+// Verlet-list rows, one thread per sorted particle i: all j in the 27
+// stencil cells with r^2 < r_list^2 (working precision), j != i; with N3L
+// only j > i.  For each of the 9 neighbouring (y, z) rows the three stencil
+// cells cx-1, cx, cx+1 are one run of consecutive sorted particles (split
+// only at a periodic x edge), walked four candidates at a time.  The 32
+// lanes of a warp are 32 consecutive sorted particles, so they span two or
+// three cells and share their runs: each load serves the lanes of one cell
+// with a single address, and no lane idles for want of a particle (a warp
+// per cell would leave about 13 of 32 lanes idle at 19 particles a cell).  Entries without an image go to the front of the
 // row in 16-byte chunks of four, padded with the sentinel index n; entries
 // with an image go to the back, one by one.  The list test needs no exact
 // image arithmetic: the list radius carries a relative margin of 2^-12, far
@@ -239,20 +241,18 @@ template <typename R, bool N3L>
 __global__ void __launch_bounds__(VL_BUILD_THREADS) k_vl_build(Dev<R> S) {
     Ctrl *C = S.ctrl;
     if (!C->rebuild_now) return;
-    const int lane = threadIdx.x & 31;
-    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (c >= S.ncell) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool act = i < S.n;
+    const int ii = act ? i : S.n - 1;
     const V4<R> *P = S.pos[C->pos_par];
     const int nx = S.nc[0], ny = S.nc[1], nz = S.nc[2];
+    const int c = S.cell_sorted[ii];
     const int cxy = c % (nx * ny);
     const int cx = cxy % nx, cy = cxy / nx, cz = c / (nx * ny);
-    const int cs = S.cell_start[c], ce = S.cell_start[c + 1];
     const int cap = S.nl_cap;
-    for (int base = cs; base < ce; base += 32) {
-        const int i = base + lane;
-        const bool act = i < ce;
-        const V4<R> pi = P[act ? i : cs];
-        uint32_t *rowp = S.nl + (size_t)(act ? i : cs) * cap;
+    {
+        const V4<R> pi = P[ii];
+        uint32_t *rowp = S.nl + (size_t)ii * cap;
         uint4 *row = reinterpret_cast<uint4 *>(rowp);
         uint32_t b0 = 0, b1 = 0, b2 = 0, b3 = 0;
         int nf = 0, nb = 0;
@@ -306,8 +306,8 @@ __global__ void __launch_bounds__(VL_BUILD_THREADS) k_vl_build(Dev<R> S) {
                     }
                     const uint32_t code = encode_image(sx, sy, sz);
                     int jb = S.cell_start[rowc + xa], je = S.cell_start[rowc + xb + 1];
-                    // does this run contain i's own cell without an image?
-                    const bool self = code == 0 && jb <= cs && cs < je;
+                    // does this run contain i itself without an image?
+                    const bool self = code == 0 && jb <= ii && ii < je;
                     const R xs = pi.x - (R)sx * S.box[0], ys = pi.y - (R)sy * S.box[1], zs = pi.z - (R)sz * S.box[2];
                     int j = jb;
                     for (; j + 4 <= je; j += 4) {
@@ -484,7 +484,7 @@ template <typename R> void launch_sortgather(const Dev<R> &S, cudaStream_t st) {
     k_sortgather<R><<<div_up((long long)S.ncell * 32, 256), 256, 0, st>>>(S);
 }
 template <typename R> void launch_vl_build(const Dev<R> &S, bool n3l, cudaStream_t st) {
-    const int blocks = div_up((long long)S.ncell * 32, VL_BUILD_THREADS);
+    const int blocks = div_up(S.n, VL_BUILD_THREADS);
     if (n3l) k_vl_build<R, true><<<blocks, VL_BUILD_THREADS, 0, st>>>(S);
     else k_vl_build<R, false><<<blocks, VL_BUILD_THREADS, 0, st>>>(S);
 }
