@@ -49,6 +49,22 @@ FP32_LANES_PER_SM = 128
 VL_STEP_TRAFFIC_1M = 619203840 + 57253376
 
 
+def max_over_ranks(ms, dist=None, device="cpu"):
+    """The slowest rank's time: every rank's figure, all-reduced with MAX."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, n_per_rank, steps, ms):
+    """Whole-job particle-steps/s of `world` independent replicas, each
+    advancing n_per_rank particles `steps` steps, timed by the slowest rank."""
+    return world * n_per_rank * steps / (ms * 1e-3)
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -360,12 +376,8 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1)
+        ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
         c1 = lj.ljsel_get_counters(hh)
-        if dist is not None:
-            tt = torch.tensor([ms], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms = float(tt.item())
         steps = c1["steps"] - c0["steps"]
         return {"ms": ms, "steps": steps, "chosen": chosen, "rep": rep,
                 "rebuilds": c1["rebuilds"] - c0["rebuilds"], "early": c1["early_rebuilds"] - c0["early_rebuilds"]}
@@ -377,7 +389,7 @@ def run_ours(args):
     for st in other:
         hx = fresh()
         r = timed(hx, st)
-        extra_runs[st] = {"value": world * n * r["steps"] / (r["ms"] * 1e-3), "chosen": r["chosen"].name(),
+        extra_runs[st] = {"value": job_throughput(world, n, r["steps"], r["ms"]), "chosen": r["chosen"].name(),
                           "tuner": r["rep"]}
         lj.ljsel_destroy(hx)
     h = fresh()
@@ -385,7 +397,7 @@ def run_ours(args):
     run = timed(h, headline)
     clocks = clk.stop()
     ms, steps_done, chosen, rep = run["ms"], run["steps"], run["chosen"], run["rep"]
-    value = world * n * steps_done / (ms * 1e-3)
+    value = job_throughput(world, n, steps_done, ms)
     chosen_name = chosen.name()
 
     # ---- per-kernel timing (CUDA events around each launch) ---------------
