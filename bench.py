@@ -217,7 +217,9 @@ def batch_leg(steps=500, warmup=5, trial_steps=10, profile_steps=30, eager=False
                        "rc 2.5, skin 0.3, R 10" % b.ntot,
            "value": b.ntot * steps / (ms * 1e-3), "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
            "graph_launches": 1, "tile": chosen.as_tuple(), "tile_costs_ms": costs, "tuning_s": tune_s,
-           "rebuilds": c1["rebuilds"] - c0["rebuilds"], "pairs_within_cutoff": npairs,
+           "rebuilds": c1["rebuilds"] - c0["rebuilds"], "early_rebuilds": c1["early_rebuilds"] - c0["early_rebuilds"],
+           "steps_counted": c1["steps"] - c0["steps"], "capacity_retries": c1["capacity_retries"],
+           "pairs_within_cutoff": npairs,
            "kernel_ms": {k: prof[k] for k in ("rebuild_ms", "force_ms", "control_ms")},
            "roofline": {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
                         "frac": ach / fp32_peak if ach else None, "traffic": None,

@@ -223,7 +223,10 @@ template <typename R> __global__ void k_bsortgather(BDev<R> S) {
 
 // Verlet list of each particle (thread per slot): every j of the 27 stencil
 // cells of its replica (periodic images of the replica's box) within the
-// list radius.  Entry = j | image code << 27, all in one segment.
+// list radius.  Row layout as for a single system: entries without an image
+// from the front in 16-byte chunks of four (the last padded with the
+// sentinel slot ntot), entries with an image (j | code << 27) from the back;
+// nl_count = front count | back count << 16.
 template <typename R> __global__ void k_bvl_build(BDev<R> S) {
     Ctrl *C = S.ctrl;
     if (!C->rebuild_now) return;
@@ -234,8 +237,11 @@ template <typename R> __global__ void k_bvl_build(BDev<R> S) {
     const V4<R> pi = P[q];
     const int lc = S.cell_sorted[q] - I.cell_off;
     const int cx = lc % I.nc[0], cy = (lc / I.nc[0]) % I.nc[1], cz = lc / (I.nc[0] * I.nc[1]);
-    uint32_t *row = S.nl + (size_t)q * S.nl_cap;
-    int cnt = 0;
+    const int cap = S.nl_cap;
+    uint32_t *row = S.nl + (size_t)q * cap;
+    uint4 *row4 = reinterpret_cast<uint4 *>(row);
+    uint32_t b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+    int nf = 0, nb = 0;
     for (int oz = -1; oz <= 1; ++oz) {
         int wz, sz;
         wrap_cell(cz, oz, I.nc[2], wz, sz);
@@ -253,19 +259,32 @@ template <typename R> __global__ void k_bvl_build(BDev<R> S) {
                     if (code == 0 && j == q) continue;
                     const V4<R> pj = P[j];
                     const R dx = pi.x - (pj.x + shx), dy = pi.y - (pj.y + shy), dz = pi.z - (pj.z + shz);
-                    if (dx * dx + dy * dy + dz * dz < S.rlist2) {
-                        if (cnt < S.nl_cap) row[cnt] = (uint32_t)j | (code << JBITS);
-                        ++cnt;
+                    if (!(dx * dx + dy * dy + dz * dz < S.rlist2)) continue;
+                    if (code == 0) {
+                        b3 = b2; b2 = b1; b1 = b0; b0 = (uint32_t)j;
+                        ++nf;
+                        if ((nf & 3) == 0 && nf + nb <= cap) row4[(nf >> 2) - 1] = make_uint4(b0, b1, b2, b3);
+                    } else {
+                        if (((nf + 4) & ~3) + nb < cap) row[cap - 1 - nb] = (uint32_t)j | (code << JBITS);
+                        ++nb;
                     }
                 }
             }
         }
     }
-    S.nl_count[q] = min(cnt, S.nl_cap);
-    if (cnt > S.nl_cap) {
-        atomicMax((unsigned long long *)&C->need_cap, (unsigned long long)cnt);
+    const int need = ((nf + 3) & ~3) + nb;
+    if (need > cap || nf > 0xffff || nb > 0xffff) {
+        atomicMax((unsigned long long *)&C->need_cap, (unsigned long long)need);
         C->overflow = 1;
+        S.nl_count[q] = 0;
+        return;
     }
+    if (nf & 3) {
+        const uint32_t sent = (uint32_t)S.ntot;
+        for (int m = nf & 3; m < 4; ++m) { b3 = b2; b2 = b1; b1 = b0; b0 = sent; }
+        row4[nf >> 2] = make_uint4(b0, b1, b2, b3);
+    }
+    S.nl_count[q] = nf | (nb << 16);
 }
 
 // ---------------------------------------------------------------------------
@@ -303,22 +322,10 @@ __global__ void __launch_bounds__(256) k_bforce(BDev<R> S, int2 *pairs3, long lo
             const RepInfo<R> &I = S.rep[rep];
             const V4<R> pi = P[i];
             const uint32_t *row = S.nl + (size_t)i * S.nl_cap;
+            const uint4 *row4 = reinterpret_cast<const uint4 *>(row);
             const int cnt = S.nl_count[i];
-            for (int k = sub; k < cnt; k += G) {
-                const uint32_t e = row[k];
-                const int j = (int)(e & JMASK);
-                const uint32_t code = e >> JBITS;
-                const V4<R> pj = P[j];
-                int sx = 0, sy = 0, sz = 0;
-                R dx, dy, dz;
-                if (code == 0) {
-                    dx = pi.x - pj.x; dy = pi.y - pj.y; dz = pi.z - pj.z;
-                } else {
-                    decode_image(code, sx, sy, sz);
-                    dx = image_dx(pi.x, pj.x, sx, I.box[0], I.box_lo[0]);
-                    dy = image_dx(pi.y, pj.y, sy, I.box[1], I.box_lo[1]);
-                    dz = image_dx(pi.z, pj.z, sz, I.box[2], I.box_lo[2]);
-                }
+            const int nq = ((cnt & 0xffff) + 3) >> 2, nb = cnt >> 16;
+            auto pair = [&](int j, int sx, int sy, int sz, R dx, R dy, R dz, const V4<R> &pj) {
                 const R r2 = r2_of(dx, dy, dz);
                 const bool in = Cut<R>::in(r2, S.rc2lo, S.rc2hi, pi, pj, sx, sy, sz, I.boxd, S.rc2d);
                 if (MODE == BMODE_PAIRS) {
@@ -329,7 +336,7 @@ __global__ void __launch_bounds__(256) k_bforce(BDev<R> S, int2 *pairs3, long lo
                             pair_rep[slot] = rep;
                         }
                     }
-                    continue;
+                    return;
                 }
                 R sr6;
                 R fr = lj_fr(r2, S.sig2, S.e24, S.e48, sr6);
@@ -339,6 +346,26 @@ __global__ void __launch_bounds__(256) k_bforce(BDev<R> S, int2 *pairs3, long lo
                     u += in ? S.e4 * sr6 * (sr6 - (R)1) - S.ushift : (R)0;
                     w += fr * r2;
                 }
+            };
+            // entries without an image: four at a time (padded with the sentinel)
+            for (int k = sub; k < nq; k += G) {
+                const uint4 e = __ldg(row4 + k);
+                const V4<R> p0 = P[e.x], p1 = P[e.y], p2 = P[e.z], p3 = P[e.w];
+                pair((int)e.x, 0, 0, 0, pi.x - p0.x, pi.y - p0.y, pi.z - p0.z, p0);
+                pair((int)e.y, 0, 0, 0, pi.x - p1.x, pi.y - p1.y, pi.z - p1.z, p1);
+                pair((int)e.z, 0, 0, 0, pi.x - p2.x, pi.y - p2.y, pi.z - p2.z, p2);
+                pair((int)e.w, 0, 0, 0, pi.x - p3.x, pi.y - p3.y, pi.z - p3.z, p3);
+            }
+            // entries with a periodic image: the exact image arithmetic
+            for (int k = sub; k < nb; k += G) {
+                const uint32_t e = row[S.nl_cap - 1 - k];
+                const int j = (int)(e & JMASK);
+                int sx, sy, sz;
+                decode_image(e >> JBITS, sx, sy, sz);
+                const V4<R> pj = P[j];
+                pair(j, sx, sy, sz, image_dx(pi.x, pj.x, sx, I.box[0], I.box_lo[0]),
+                     image_dx(pi.y, pj.y, sy, I.box[1], I.box_lo[1]), image_dx(pi.z, pj.z, sz, I.box[2], I.box_lo[2]),
+                     pj);
             }
         }
         if (MODE == BMODE_PAIRS) continue;
@@ -598,7 +625,7 @@ struct ljsel_batch_s {
 
     ljsel_status grow() {
         const long long need = h_ctrl->need_cap;
-        nl_cap = (int)std::max<long long>(need + need / 5 + 8, nl_cap + 16);
+        nl_cap = (int)((std::max<long long>(need + need / 5 + 8, nl_cap + 16) + 3) & ~3LL);
         retries += 1;
         if (retries > 64) { set_error("batch neighbour lists keep overflowing"); return LJSEL_ERR_CAPACITY; }
         TRY(b_nl.ensure((size_t)nl_cap * ntot * 4));
@@ -835,7 +862,7 @@ ljsel_status ljsel_batch_create(const ljsel_params *params, int32_t nrep, const 
     for (int r = 0; r < nrep; ++r)
         rho_max = std::max(rho_max, counts[r] / (boxes[3 * r] * boxes[3 * r + 1] * boxes[3 * r + 2]));
     const double rl = params->rcut[0] + params->skin;
-    b->nl_cap = (int)std::min(4.18879 * rl * rl * rl * rho_max * 1.35 + 16, 4096.0);
+    b->nl_cap = ((int)std::min(4.18879 * rl * rl * rl * rho_max * 1.35 + 16, 4096.0) + 3) & ~3;
     const size_t n = (size_t)ntot, n3 = n * 3 * sizeof(double);
     std::vector<int> rep_of(n);
     for (int r = 0; r < nrep; ++r)
