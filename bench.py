@@ -219,6 +219,7 @@ def batch_leg(steps=500, warmup=5, trial_steps=10, profile_steps=30, eager=False
            "graph_launches": 1, "tile": chosen.as_tuple(), "tile_costs_ms": costs, "tuning_s": tune_s,
            "rebuilds": c1["rebuilds"] - c0["rebuilds"], "early_rebuilds": c1["early_rebuilds"] - c0["early_rebuilds"],
            "steps_counted": c1["steps"] - c0["steps"], "capacity_retries": c1["capacity_retries"],
+           "replica_rebuilds": c1["replica_rebuilds"] - c0["replica_rebuilds"],
            "pairs_within_cutoff": npairs,
            "kernel_ms": {k: prof[k] for k in ("rebuild_ms", "force_ms", "control_ms")},
            "roofline": {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
@@ -259,7 +260,7 @@ def inhomogeneous_leg(steps=20000, every=1000, strategy="predictive", fixed_step
 
     def tuned_run():
         for k in range(steps // every):
-            c, rep = s.autotune(strategy=strategy, trial_steps=10, probe_steps=2, probe_factor=2.0,
+            c, rep = s.autotune(strategy=strategy, trial_steps=5, probe_steps=2, probe_factor=2.0,
                                 skip_within=skip_within)
             s.step(every - rep["trial_steps_total"])
             phases.append({"step": k * every, "chosen": c.name(), "ntrialled": rep["ntrialled"],
@@ -526,7 +527,7 @@ def main():
     ap.add_argument("--newton3", action="store_true")
     ap.add_argument("--tpu", type=int, default=1)
     ap.add_argument("--cluster", type=int, default=8)
-    ap.add_argument("--trial-steps", type=int, default=10)
+    ap.add_argument("--trial-steps", type=int, default=5)
     ap.add_argument("--probe-steps", type=int, default=2)
     ap.add_argument("--strategy", default="expert", choices=["full", "predictive", "expert"],
                     help="tuning strategy of the headline run (the other of expert/full is reported beside it)")

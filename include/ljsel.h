@@ -125,6 +125,9 @@ typedef struct ljsel_counters {
     int64_t nclusters;         /* i-clusters (CLUSTER)                         */
     int64_t ncells;            /* cells of the current grid                    */
     int64_t capacity_retries;  /* list reallocations after an overflow         */
+    int64_t replica_rebuilds;  /* batches: replica rebuilds summed over all
+                                  replicas (each rebuild event re-lists only
+                                  the replicas that need it); 0 otherwise     */
 } ljsel_counters;
 
 /* Autotuner options (Sec. 2.2.5 Full Search, Sec. 5.1 Predictive, Sec. 5.2

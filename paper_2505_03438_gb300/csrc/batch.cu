@@ -11,11 +11,14 @@
 // cells of replica 0, then replica 1, ...; so the replica of a slot never
 // changes and is looked up from a static table.
 //
-// Per step (Sec. 2.1, Sec. 2.2.1): IF(rebuild) {bin -> scan -> scatter ->
-// sort + gather -> Verlet lists -> finish}, then the fused force + Stormer-
-// Verlet kernel, then the control kernel (the same rebuild rule as a single
-// system: every R steps, or as soon as any particle of any replica moved
-// skin/2).  The force kernel takes a "tile": lanes per particle and CTA
+// Per step (Sec. 2.1, Sec. 2.2.1): IF(rebuild) {plan -> bin -> scan ->
+// scatter -> sort + gather -> Verlet lists -> finish}, then the fused force +
+// Stormer-Verlet kernel, then the control kernel.  The Verlet-list rule is
+// kept per replica: a rebuild event happens as soon as any particle of any
+// replica moved skin/2 (or R steps after the last event), and it re-bins and
+// re-lists only the replicas that need it -- those with a particle at skin/2,
+// or R steps or more since their own last rebuild; the others keep their
+// slots, cells and lists.  The force kernel takes a "tile": lanes per particle and CTA
 // size, optionally as a persistent grid that strides over the tiles; the
 // batch autotuner times the tiles and keeps the fastest.
 #include <algorithm>
@@ -72,7 +75,12 @@ template <typename R> struct BDev {
     V4<R> *pos[2];  // [ntot + 1], slot ntot is a sentinel
     V4<R> *xref;
     V4<R> *force;
-    int *cell_count, *cell_start, *cell_of, *slot_of, *cell_sorted, *tmp_idx, *tmp_key, *block_sum;
+    int *cell_count, *cell_start, *cell_of, *slot_of, *cell_sorted, *tmp_idx, *tmp_key;
+    const int *cell_rep;     // [ncell] replica of each cell (static)
+    int *rep_flag;           // [nrep] a particle of the replica moved skin/2
+    int *rep_do;             // [nrep] the replica is rebuilt in this event
+    long long *rep_last;     // [nrep] step of the replica's last rebuild
+    int interval;            // R
     uint32_t *nl;
     int *nl_count;
     int nl_cap;
@@ -86,7 +94,23 @@ template <typename R> struct BDev {
 // ---------------------------------------------------------------------------
 // Rebuild
 
-// Bin every particle into its replica's grid.  The FP64 position is first
+// Which replicas this rebuild event covers; resets their flags.
+template <typename R> __global__ void k_bplan(BDev<R> S) {
+    Ctrl *C = S.ctrl;
+    if (!C->rebuild_now) return;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= S.nrep) return;
+    const long long now = C->total_steps;
+    const bool go = C->rebuild_all || S.rep_flag[r] || now - S.rep_last[r] >= S.interval;
+    S.rep_do[r] = go ? 1 : 0;
+    if (go) {
+        S.rep_flag[r] = 0;
+        S.rep_last[r] = now;
+        atomicAdd((unsigned long long *)&C->replica_rebuilds, 1ull);
+    }
+}
+
+// Bin every particle of a replica being rebuilt into its replica's grid.  The FP64 position is first
 // wrapped into the replica's box (positions drift out of it between
 // rebuilds), so that the image shift a cell stencil implies is the image
 // shift of the stored coordinates.
@@ -96,7 +120,9 @@ template <typename R> __global__ void k_bbin(BDev<R> S) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g == 0) { C->need_cap = 0; C->overflow = 0; }
     if (g >= S.ntot) return;
-    const RepInfo<R> &I = S.rep[S.rep_of[g]];
+    const int rep = S.rep_of[g];
+    if (!S.rep_do[rep]) return;
+    const RepInfo<R> &I = S.rep[rep];
     double *X = S.x[C->state_par];
     int c3[3];
     bool bad = false;
@@ -117,9 +143,8 @@ template <typename R> __global__ void k_bbin(BDev<R> S) {
     S.slot_of[g] = atomicAdd(&S.cell_count[cell], 1);
 }
 
-// Exclusive scan of the cell counts in three passes: per-block sums, a scan
-// of the block sums by one block, and the final offsets (which also clear the
-// counts for the next rebuild).
+// Inclusive scan of one value per thread over a CTA (warp shuffles, then
+// the warp totals by the first warp).
 __device__ __forceinline__ int block_incl_scan(int v, int *sh) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int o = 1; o < 32; o <<= 1) {
@@ -140,25 +165,31 @@ __device__ __forceinline__ int block_incl_scan(int v, int *sh) {
     return v + (warp > 0 ? sh[warp - 1] : 0);
 }
 
-template <typename R> __global__ void __launch_bounds__(SCAN_BLOCK) k_bscan_sums(BDev<R> S) {
-    if (!S.ctrl->rebuild_now) return;
-    __shared__ int sh[32];
-    const int c = blockIdx.x * SCAN_BLOCK + threadIdx.x;
-    const int v = c < S.ncell ? S.cell_count[c] : 0;
-    const int incl = block_incl_scan(v, sh);
-    if (threadIdx.x == SCAN_BLOCK - 1) S.block_sum[blockIdx.x] = incl;
-}
-
-template <typename R> __global__ void __launch_bounds__(SCAN_BLOCK) k_bscan_top(BDev<R> S, int nblocks) {
-    if (!S.ctrl->rebuild_now) return;
+// Per-replica exclusive scan of the cell counts of the replicas being
+// rebuilt: one CTA per replica, starting at the replica's first slot; the
+// counts are cleared for the next event.  Other replicas keep their starts.
+template <typename R> __global__ void __launch_bounds__(SCAN_BLOCK) k_bscan_rep(BDev<R> S) {
+    Ctrl *C = S.ctrl;
+    if (!C->rebuild_now) return;
+    const int r = blockIdx.x;
+    if (r == 0 && threadIdx.x == 0) {
+        S.cell_start[S.ncell] = S.ntot;
+        C->rebuild_all = 0;  // the plan kernel, which read it, has finished
+    }
+    if (!S.rep_do[r]) return;
     __shared__ int sh[32];
     __shared__ int total;
-    int carry = 0;
-    for (int base = 0; base < nblocks; base += SCAN_BLOCK) {
+    const RepInfo<R> &I = S.rep[r];
+    const int c0 = I.cell_off, nc = I.nc[0] * I.nc[1] * I.nc[2];
+    int carry = I.p_off;
+    for (int base = 0; base < nc; base += SCAN_BLOCK) {
         const int k = base + threadIdx.x;
-        const int v = k < nblocks ? S.block_sum[k] : 0;
+        const int v = k < nc ? S.cell_count[c0 + k] : 0;
         const int incl = block_incl_scan(v, sh);
-        if (k < nblocks) S.block_sum[k] = carry + incl - v;  // exclusive
+        if (k < nc) {
+            S.cell_start[c0 + k] = carry + incl - v;
+            S.cell_count[c0 + k] = 0;
+        }
         if (threadIdx.x == SCAN_BLOCK - 1) total = incl;
         __syncthreads();
         carry += total;
@@ -166,24 +197,12 @@ template <typename R> __global__ void __launch_bounds__(SCAN_BLOCK) k_bscan_top(
     }
 }
 
-template <typename R> __global__ void __launch_bounds__(SCAN_BLOCK) k_bscan_final(BDev<R> S) {
-    if (!S.ctrl->rebuild_now) return;
-    __shared__ int sh[32];
-    const int c = blockIdx.x * SCAN_BLOCK + threadIdx.x;
-    const int v = c < S.ncell ? S.cell_count[c] : 0;
-    const int incl = block_incl_scan(v, sh);
-    if (c < S.ncell) {
-        S.cell_start[c] = S.block_sum[blockIdx.x] + incl - v;
-        S.cell_count[c] = 0;
-    }
-    if (c == 0) S.cell_start[S.ncell] = S.ntot;
-}
-
 template <typename R> __global__ void k_bscatter(BDev<R> S) {
     Ctrl *C = S.ctrl;
     if (!C->rebuild_now) return;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= S.ntot) return;
+    if (!S.rep_do[S.rep_of[g]]) return;
     const int dst = S.cell_start[S.cell_of[g]] + S.slot_of[g];
     S.tmp_idx[dst] = g;
     S.tmp_key[dst] = S.id[C->state_par][g];
@@ -213,6 +232,19 @@ template <typename R> __global__ void k_bsortgather(BDev<R> S) {
     if (cell >= S.ncell) return;
     const int sp = C->state_par, pp = C->pos_par;
     const int start = S.cell_start[cell], m = S.cell_start[cell + 1] - start;
+    if (!S.rep_do[S.cell_rep[cell]]) {
+        // a replica not rebuilt keeps its slots: carry its state over to the
+        // buffer that becomes current
+        const int n = S.ntot;
+        for (int q = start + lane; q < start + m; q += 32) {
+            for (int d = 0; d < 3; ++d) {
+                S.x[sp ^ 1][d * n + q] = S.x[sp][d * n + q];
+                S.v[sp ^ 1][d * n + q] = S.v[sp][d * n + q];
+            }
+            S.id[sp ^ 1][q] = S.id[sp][q];
+        }
+        return;
+    }
     for (int e = lane; e < ((m + 31) & ~31); e += 32) {
         const int key = e < m ? S.tmp_key[start + e] : 0x7fffffff;
         int rank = 0;
@@ -232,6 +264,7 @@ template <typename R> __global__ void k_bvl_build(BDev<R> S) {
     if (!C->rebuild_now) return;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= S.ntot) return;
+    if (!S.rep_do[S.rep_of[q]]) return;
     const V4<R> *P = S.pos[C->pos_par];
     const RepInfo<R> &I = S.rep[S.rep_of[q]];
     const V4<R> pi = P[q];
@@ -393,7 +426,10 @@ __global__ void __launch_bounds__(256) k_bforce(BDev<R> S, int2 *pairs3, long lo
         S.pos[pp ^ 1][i] = nw;
         const V4<R> r0 = S.xref[i];
         const R ddx = nw.x - r0.x, ddy = nw.y - r0.y, ddz = nw.z - r0.z;
-        exceeded = exceeded || !(ddx * ddx + ddy * ddy + ddz * ddz < S.half_skin2);
+        if (!(ddx * ddx + ddy * ddy + ddz * ddz < S.half_skin2)) {
+            exceeded = true;
+            S.rep_flag[rep] = 1;
+        }
         bad = bad || !isfinite(fx + fy + fz);
     }
     if (MODE == BMODE_STEP) {
@@ -464,7 +500,7 @@ template <typename R> __global__ void k_bsync(BDev<R> S) {
 
 __global__ void k_bcmd(Ctrl *C, int op, long long a) {
     switch (op) {
-        case CMD_REBUILD: C->rebuild_now = 1; break;
+        case CMD_REBUILD: C->rebuild_now = 1; C->rebuild_all = 1; break;
         case CMD_BEGIN: C->steps_done = 0; C->steps_target = a; break;
         case CMD_RESET_PAIRS: C->npairs = 0; break;
         case CMD_HALF_KICK: C->half_kick = (int)a; break;
@@ -501,7 +537,8 @@ struct ljsel_batch_s {
     std::vector<int> counts, p_off, cell_off;
     std::vector<double> boxes;
     Buf b_rep, b_rep_of, b_x[2], b_v[2], b_id[2], b_pos[2], b_xref, b_force, b_cell_count, b_cell_start, b_cell_of,
-        b_slot_of, b_cell_sorted, b_tmp_idx, b_tmp_key, b_block_sum, b_nl, b_nl_count, b_ctrl, b_ev, b_io;
+        b_slot_of, b_cell_sorted, b_tmp_idx, b_tmp_key, b_nl, b_nl_count, b_ctrl, b_ev, b_io, b_cell_rep,
+        b_rep_flag, b_rep_do, b_rep_last;
     Ctrl *h_ctrl = nullptr;
     bool synced = true;
     long long retries = 0;
@@ -519,7 +556,7 @@ struct ljsel_batch_s {
     std::vector<Buf *> bufs() {
         return {&b_rep, &b_rep_of, &b_x[0], &b_x[1], &b_v[0], &b_v[1], &b_id[0], &b_id[1], &b_pos[0], &b_pos[1],
                 &b_xref, &b_force, &b_cell_count, &b_cell_start, &b_cell_of, &b_slot_of, &b_cell_sorted, &b_tmp_idx,
-                &b_tmp_key, &b_block_sum, &b_nl, &b_nl_count, &b_ctrl, &b_ev, &b_io};
+                &b_tmp_key, &b_nl, &b_nl_count, &b_ctrl, &b_ev, &b_io, &b_cell_rep, &b_rep_flag, &b_rep_do, &b_rep_last};
     }
     size_t p4() const { return precision ? sizeof(D4) : sizeof(float4); }
 
@@ -545,7 +582,11 @@ struct ljsel_batch_s {
         S.cell_sorted = (int *)b_cell_sorted.ptr;
         S.tmp_idx = (int *)b_tmp_idx.ptr;
         S.tmp_key = (int *)b_tmp_key.ptr;
-        S.block_sum = (int *)b_block_sum.ptr;
+        S.cell_rep = (const int *)b_cell_rep.ptr;
+        S.rep_flag = (int *)b_rep_flag.ptr;
+        S.rep_do = (int *)b_rep_do.ptr;
+        S.rep_last = (long long *)b_rep_last.ptr;
+        S.interval = interval;
         S.nl = (uint32_t *)b_nl.ptr;
         S.nl_count = (int *)b_nl_count.ptr;
         S.nl_cap = nl_cap;
@@ -583,11 +624,9 @@ struct ljsel_batch_s {
     }
 
     template <typename R> void enqueue_rebuild(const BDev<R> &S, cudaStream_t st) const {
-        const int nb = (ncell + SCAN_BLOCK - 1) / SCAN_BLOCK;
+        k_bplan<R><<<div_up(nrep, 256), 256, 0, st>>>(S);
         k_bbin<R><<<div_up(ntot, 256), 256, 0, st>>>(S);
-        k_bscan_sums<R><<<nb, SCAN_BLOCK, 0, st>>>(S);
-        k_bscan_top<R><<<1, SCAN_BLOCK, 0, st>>>(S, nb);
-        k_bscan_final<R><<<nb, SCAN_BLOCK, 0, st>>>(S);
+        k_bscan_rep<R><<<nrep, SCAN_BLOCK, 0, st>>>(S);
         k_bscatter<R><<<div_up(ntot, 256), 256, 0, st>>>(S);
         k_bsortgather<R><<<div_up((long long)ncell * 32, 256), 256, 0, st>>>(S);
         k_bvl_build<R><<<div_up(ntot, 128), 128, 0, st>>>(S);
@@ -868,18 +907,25 @@ ljsel_status ljsel_batch_create(const ljsel_params *params, int32_t nrep, const 
     for (int r = 0; r < nrep; ++r)
         for (int k = b->p_off[r]; k < b->p_off[r + 1]; ++k) rep_of[k] = r;
     const size_t cells1 = (size_t)b->ncell + 1;
-    const int nblocks = (b->ncell + SCAN_BLOCK - 1) / SCAN_BLOCK;
     struct { Buf *b; size_t bytes; } plan[] = {
         {&b->b_rep_of, n * 4}, {&b->b_x[0], n3}, {&b->b_x[1], n3}, {&b->b_v[0], n3}, {&b->b_v[1], n3},
         {&b->b_id[0], n * 4}, {&b->b_id[1], n * 4}, {&b->b_pos[0], (n + 1) * b->p4()}, {&b->b_pos[1], (n + 1) * b->p4()},
         {&b->b_xref, n * b->p4()}, {&b->b_force, n * b->p4()}, {&b->b_cell_count, cells1 * 4},
         {&b->b_cell_start, cells1 * 4}, {&b->b_cell_of, n * 4}, {&b->b_slot_of, n * 4}, {&b->b_cell_sorted, n * 4},
-        {&b->b_tmp_idx, n * 4}, {&b->b_tmp_key, n * 4}, {&b->b_block_sum, (size_t)(nblocks + 1) * 4},
+        {&b->b_tmp_idx, n * 4}, {&b->b_tmp_key, n * 4}, {&b->b_cell_rep, cells1 * 4},
+        {&b->b_rep_flag, (size_t)nrep * 4}, {&b->b_rep_do, (size_t)nrep * 4}, {&b->b_rep_last, (size_t)nrep * 8},
         {&b->b_nl, (size_t)b->nl_cap * n * 4}, {&b->b_nl_count, n * 4}, {&b->b_ctrl, sizeof(Ctrl)},
         {&b->b_ev, 2 * (size_t)nrep * sizeof(double)}};
     for (auto &p : plan)
         if ((st = p.b->ensure(p.bytes)) != LJSEL_OK) return fail(st);
+    std::vector<int> cell_rep(cells1, nrep - 1);
+    for (int r = 0; r < nrep; ++r)
+        for (int c = b->cell_off[r]; c < b->cell_off[r + 1]; ++c) cell_rep[c] = r;
     if (cudaMemcpy(b->b_rep_of.ptr, rep_of.data(), n * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->b_cell_rep.ptr, cell_rep.data(), cells1 * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(b->b_rep_flag.ptr, 0, (size_t)nrep * 4) != cudaSuccess ||
+        cudaMemset(b->b_rep_do.ptr, 0, (size_t)nrep * 4) != cudaSuccess ||
+        cudaMemset(b->b_rep_last.ptr, 0, (size_t)nrep * 8) != cudaSuccess ||
         cudaMemset(b->b_cell_count.ptr, 0, cells1 * 4) != cudaSuccess ||
         cudaMemset(b->b_ctrl.ptr, 0, sizeof(Ctrl)) != cudaSuccess ||
         cudaMemset(b->b_nl_count.ptr, 0, n * 4) != cudaSuccess) {
@@ -1149,6 +1195,7 @@ ljsel_status ljsel_batch_get_counters(ljsel_batch b, ljsel_counters *c) {
     c->list_capacity = (int64_t)b->nl_cap * b->ntot;
     c->ncells = b->ncell;
     c->capacity_retries = b->retries;
+    c->replica_rebuilds = b->h_ctrl->replica_rebuilds;
     return LJSEL_OK;
 }
 

@@ -99,8 +99,9 @@ struct Ctrl {
     int64_t list_entries;      // entries written by the last list build
     unsigned long long npairs; // pair-export counter
     int32_t scan_ticket;
-    int32_t pad2;
+    int32_t rebuild_all;       // batches: the next rebuild covers every replica
     double epot, virial, ekin; // FP64 sums
+    int64_t replica_rebuilds;  // batches: replica rebuilds summed over replicas
 };
 
 // Everything a kernel needs, passed by value.

@@ -103,6 +103,8 @@ def test_batch_fp64_trajectories_match_oracle():
         assert np.abs(vr - vo).max() < 1e-9, r
     c = b.counters()
     assert c["steps"] == 60 and c["rebuilds"] >= 6
+    # each event re-lists only the replicas that need it
+    assert c["replica_rebuilds"] < len(reps) * c["rebuilds"], c
 
 
 def test_batch_fp32_tracks_fp64_and_conserves_energy():
