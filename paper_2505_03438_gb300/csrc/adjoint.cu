@@ -198,6 +198,110 @@ __global__ void __launch_bounds__(VJP_THREADS) k_vjp(Dev<R> S, const V4<R> *cot,
     }
 }
 
+// The same VJP over the Verlet-list rows (configuration VL without N3L:
+// full rows, entries without an image in 16-byte chunks padded with the
+// sentinel, image entries at the back).  The list holds every pair within
+// r_c + skin; the exact cutoff decision keeps the in-range ones, so the mask
+// is the force kernels' mask.
+template <typename R, int G>
+__global__ void __launch_bounds__(VJP_THREADS) k_vjp_vl(Dev<R> S, const V4<R> *cot, double *gx, int accumulate,
+                                                       double *theta) {
+    __shared__ double red[2 * MAXT2];
+    for (int k = threadIdx.x; k < 2 * MAXT2; k += blockDim.x) red[k] = 0.0;
+    __syncthreads();
+    const Ctrl *C = S.ctrl;
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = gid / G, sub = gid % G;
+    const bool valid = i < S.n;
+    const int pp = C->pos_par, sp = C->state_par, nt = S.tab.ntypes;
+    const V4<R> *P = S.pos[pp];
+    R ge[MAXT], gs[MAXT];
+#pragma unroll
+    for (int k = 0; k < MAXT; ++k) { ge[k] = 0; gs[k] = 0; }
+    R gxx = 0, gxy = 0, gxz = 0;
+    int ti = 0;
+    if (valid) {
+        const V4<R> pi = ldpos(P, i);
+        const V4<R> ci = cot[i];
+        ti = type_of(pi);
+        const uint32_t *row = S.nl + (size_t)i * S.nl_cap;
+        const uint4 *row4 = reinterpret_cast<const uint4 *>(row);
+        const int cnt = S.nl_count[i];
+        const int nq = ((cnt & 0xffff) + 3) >> 2, nb = cnt >> 16;
+        auto pair = [&](int j, int sx, int sy, int sz, R dx, R dy, R dz, const V4<R> &pj) {
+            const R r2 = r2_of(dx, dy, dz);
+            const int tj = type_of(pj);
+            const int tp = ti * nt + tj;
+            if (!Cut<R>::in(r2, S.tab.rc2lo[tp], S.tab.rc2hi[tp], pi, pj, sx, sy, sz, S.boxd, S.tab.rc2d[tp])) return;
+            const R e24 = S.tab.e24[tp];
+            const R rinv2 = fast_rcp(r2);
+            const R sr2 = S.tab.sig2[tp] * rinv2;
+            const R q = sr2 * sr2 * sr2;
+            const R a = rinv2 * q;
+            const R g = a * (S.tab.e48[tp] * q - e24);
+            const R dgds = a * rinv2 * e24 * ((R)4 - (R)14 * q);
+            const V4<R> cj = cot[j];
+            const R ux = ci.x - cj.x, uy = ci.y - cj.y, uz = ci.z - cj.z;
+            const R ur = ux * dx + uy * dy + uz * dz;
+            const R k2 = (R)2 * dgds * ur;
+            gxx += g * ux + k2 * dx;
+            gxy += g * uy + k2 * dy;
+            gxz += g * uz + k2 * dz;
+            const R t1 = ur * a;
+            const R de = t1 * ((R)48 * q - (R)24);
+            const R dsg = t1 * (R)6 * e24 * S.tab.inv_sig[tp] * ((R)4 * q - (R)1);
+#pragma unroll
+            for (int k = 0; k < MAXT; ++k)
+                if (k == tj) { ge[k] += de; gs[k] += dsg; }
+        };
+        for (int k = sub; k < nq; k += G) {
+            const uint4 e = __ldg(row4 + k);
+            const V4<R> p0 = ldpos(P, (int)e.x), p1 = ldpos(P, (int)e.y), p2 = ldpos(P, (int)e.z), p3 = ldpos(P, (int)e.w);
+            pair((int)e.x, 0, 0, 0, pi.x - p0.x, pi.y - p0.y, pi.z - p0.z, p0);
+            pair((int)e.y, 0, 0, 0, pi.x - p1.x, pi.y - p1.y, pi.z - p1.z, p1);
+            pair((int)e.z, 0, 0, 0, pi.x - p2.x, pi.y - p2.y, pi.z - p2.z, p2);
+            pair((int)e.w, 0, 0, 0, pi.x - p3.x, pi.y - p3.y, pi.z - p3.z, p3);
+        }
+        for (int k = sub; k < nb; k += G) {
+            const uint32_t e = row[S.nl_cap - 1 - k];
+            const int j = (int)(e & JMASK);
+            int sx, sy, sz;
+            decode_image(e >> JBITS, sx, sy, sz);
+            const V4<R> pj = ldpos(P, j);
+            pair(j, sx, sy, sz, image_dx(pi.x, pj.x, sx, S.box[0], S.box_lo[0]),
+                 image_dx(pi.y, pj.y, sy, S.box[1], S.box_lo[1]), image_dx(pi.z, pj.z, sz, S.box[2], S.box_lo[2]), pj);
+        }
+    }
+    gxx = group_sum<R, G>(gxx);
+    gxy = group_sum<R, G>(gxy);
+    gxz = group_sum<R, G>(gxz);
+#pragma unroll
+    for (int k = 0; k < MAXT; ++k) {
+        ge[k] = group_sum<R, G>(ge[k]);
+        gs[k] = group_sum<R, G>(gs[k]);
+    }
+    if (valid && sub == 0) {
+        const int id = S.id[sp][i];
+        if (accumulate) {
+            gx[3 * id + 0] += (double)gxx; gx[3 * id + 1] += (double)gxy; gx[3 * id + 2] += (double)gxz;
+        } else {
+            gx[3 * id + 0] = (double)gxx; gx[3 * id + 1] = (double)gxy; gx[3 * id + 2] = (double)gxz;
+        }
+#pragma unroll
+        for (int k = 0; k < MAXT; ++k) {
+            if (k < nt) {
+                atomicAdd(&red[ti * nt + k], (double)ge[k]);
+                atomicAdd(&red[MAXT2 + ti * nt + k], (double)gs[k]);
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < nt * nt) {
+        atomicAdd(&theta[threadIdx.x], red[threadIdx.x]);
+        atomicAdd(&theta[MAXT2 + threadIdx.x], red[MAXT2 + threadIdx.x]);
+    }
+}
+
 template <typename F> ljsel_status dispatch(System *s, F &&f) {
     if (s->precision) return f((double)0);
     return f((float)0);
@@ -241,14 +345,20 @@ ljsel_status vjp_level(System *s, const double *src, double *vbar, const double 
     int G = 1;
     while (G < 32 && (long long)s->n * G < 152LL * 2048) G *= 2;
     const int grid = div_up((long long)s->n * G, VJP_THREADS);
+    // full Verlet-list rows when the configuration has them, else the cells
+    const bool rows = s->cfg.method == LJSEL_METHOD_VL && !s->cfg.newton3;
+#define VJP_GO(g)                                                                               \
+    (rows ? k_vjp_vl<R, g><<<grid, VJP_THREADS, 0, s->stream>>>(S, cot, gx, accumulate, th)     \
+          : k_vjp<R, g><<<grid, VJP_THREADS, 0, s->stream>>>(S, cot, gx, accumulate, th))
     switch (G) {
-        case 1: k_vjp<R, 1><<<grid, VJP_THREADS, 0, s->stream>>>(S, cot, gx, accumulate, th); break;
-        case 2: k_vjp<R, 2><<<grid, VJP_THREADS, 0, s->stream>>>(S, cot, gx, accumulate, th); break;
-        case 4: k_vjp<R, 4><<<grid, VJP_THREADS, 0, s->stream>>>(S, cot, gx, accumulate, th); break;
-        case 8: k_vjp<R, 8><<<grid, VJP_THREADS, 0, s->stream>>>(S, cot, gx, accumulate, th); break;
-        case 16: k_vjp<R, 16><<<grid, VJP_THREADS, 0, s->stream>>>(S, cot, gx, accumulate, th); break;
-        default: k_vjp<R, 32><<<grid, VJP_THREADS, 0, s->stream>>>(S, cot, gx, accumulate, th); break;
+        case 1: VJP_GO(1); break;
+        case 2: VJP_GO(2); break;
+        case 4: VJP_GO(4); break;
+        case 8: VJP_GO(8); break;
+        case 16: VJP_GO(16); break;
+        default: VJP_GO(32); break;
     }
+#undef VJP_GO
     CK(cudaGetLastError());
     return LJSEL_OK;
 }

@@ -48,11 +48,17 @@ def _case(size):
 
 
 @pytest.mark.parametrize("precision", [1, 0], ids=["fp64", "fp32"])
-@pytest.mark.parametrize("size", ["small", "full"])
-def test_force_vjp_matches_oracle(size, precision):
+@pytest.mark.parametrize("size,cfg", [("small", None), ("full", None), ("small", dict(method="LC")),
+                                      ("full", dict(method="LC")), ("small", dict(method="VL", newton3=True))],
+                         ids=["small-rows", "full-rows", "small-cells", "full-cells", "small-n3l-cells"])
+def test_force_vjp_matches_oracle(size, cfg, precision):
+    """Verlet-list rows (VL without N3L) and the cell traversal (every other
+    configuration) give the same VJP as the oracle."""
     sc = _case(size)
     x, types = sc["x"], sc["types"]
     s = lj.System(sc, precision=precision)
+    if cfg:
+        s.set_config(rebuild_interval=10, **cfg)
     c = np.random.default_rng(21).normal(size=x.shape)
     g, ge, gs = s.force_vjp(c)
     xo = x if precision else _f32(x)  # the positions the GPU pair arithmetic works on
