@@ -463,7 +463,21 @@ template <typename R> ljsel_status System::ensure_structure() {
         LJ_CUDA(cudaGetLastError());
         LJ_TRY(read_ctrl());
         LJ_TRY(check_device_errors());
-        if (!h_ctrl->overflow) return LJSEL_OK;
+        if (!h_ctrl->overflow) {
+            // Verlet-list rows have a fixed capacity set from the mean density;
+            // once a build has measured the longest row, the capacity is fitted
+            // to it (with room for its fluctuation), so that the force kernel's
+            // prefetch of a block's rows carries little unused capacity.
+            const long long need = h_ctrl->need_cap;
+            if (cfg.method == LJSEL_METHOD_VL && !cap_fitted && need > 0 && nl_cap > need + need / 8 + 16) {
+                cap_fitted = true;
+                nl_cap = (int)((need + need / 16 + 8 + 3) & ~3LL);
+                LJ_TRY(apply_config());
+                LJ_TRY(cmd(CMD_REBUILD, 0));
+                continue;
+            }
+            return LJSEL_OK;
+        }
         LJ_TRY(handle_overflow());
     }
     set_error("neighbour structure could not be built");

@@ -56,6 +56,7 @@ struct System {
     int nl_cap = 0;
     int ncl_cap = 0, cp_cap = 0, cp_stride = 0;
     long long capacity_retries = 0;
+    bool cap_fitted = false;  // the Verlet-list row capacity was fitted to a build
     bool structure_dirty = true;
     bool synced = true;  // velocities at the integer step
     // device buffers
