@@ -43,10 +43,11 @@ FLOPS_PER_PAIR = 28
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of one launch of the Verlet-list force kernel
-# fused with the update (N3L off), N = 1,048,576, from the ncu capture
-# summarised in profiles/liquid_1m_force_vl_ncu.md.  Valid only for that
-# kernel at that size; reported as null for any other chosen configuration.
-VL_STEP_TRAFFIC_1M = 619203840 + 57253376
+# fused with the update (N3L off, two lanes per particle, fitted row
+# capacity), N = 1,048,576, from the ncu capture summarised in
+# profiles/liquid_1m_force_vl_ncu.md.  Valid only for that kernel at that
+# size; reported as null for any other chosen configuration.
+VL_STEP_TRAFFIC_1M = 491804928 + 58008832
 
 
 def max_over_ranks(ms, dist=None, device="cpu"):
@@ -468,10 +469,11 @@ def run_ours(args):
     force_ms = prof["force_ms"]
     achieved = npairs * FLOPS_PER_PAIR / (force_ms * 1e-3) / 1e12 if force_ms > 0 else None
     hbm = peaks.get("hbm_gbs", 6800.0)
-    traffic = VL_STEP_TRAFFIC_1M if (chosen.method == lj.METHOD_VL and not chosen.newton3 and n == 1048576) else None
+    traffic = VL_STEP_TRAFFIC_1M if (chosen.method == lj.METHOD_VL and not chosen.newton3 and
+                                     chosen.threads_per_unit == 2 and n == 1048576) else None
     roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": (achieved / fp32_peak) if achieved else None, "traffic": traffic,
-            "binding_unit": "L1 gather throughput (76.8 % of peak in ncu); DRAM 42 %, issue 43 %",
+            "binding_unit": "L1 gather throughput (84 % of peak in ncu, VL two lanes); DRAM 45 %, issue 48 %",
             "kernel": "force (%s)" % chosen_name, "launch_ms": force_ms, "flops_per_launch": npairs * FLOPS_PER_PAIR,
             "peak_basis": "152 SMs x 128 FP32 lanes x 2 x %g MHz (of measured max clock)" % sm_max}
     cb = None
