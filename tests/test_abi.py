@@ -76,6 +76,27 @@ def test_invalid_arguments_fail_without_gpu(built):
     with pytest.raises(built.LjselError) as e:
         built.ljsel_create(p, 4, x, x)
     assert e.value.status == 1
+    # more particles than a 27-bit list index can name
+    p = built.make_params(box=20.0)
+    with pytest.raises(built.LjselError) as e:
+        built.ljsel_create(p, 1 << 27, x, x)
+    assert e.value.status == 1
+    # batches: one species only; every replica box at least 2 (r_c + skin); counts >= 0
+    boxes = np.full((2, 3), 20.0)
+    with pytest.raises(built.LjselError) as e:
+        built.ljsel_batch_create(built.make_params(20.0, eps=[[1, 1], [1, 1]], sigma=[[1, 1], [1, 1]]), boxes,
+                                 [2, 2], x, x)
+    assert e.value.status == 9
+    with pytest.raises(built.LjselError) as e:
+        built.ljsel_batch_create(built.make_params(20.0), np.array([[20.0] * 3, [5.0] * 3]), [2, 2], x, x)
+    assert e.value.status == 5
+    with pytest.raises(built.LjselError) as e:
+        built.ljsel_batch_create(built.make_params(20.0), boxes, [5, -1], x, x)
+    assert e.value.status == 1
+
+
+def test_batch_tile_layout(built):
+    assert ctypes.sizeof(built.ljsel_batch_tile) == 16
 
 
 def test_missing_library_fails_loudly(monkeypatch, built):

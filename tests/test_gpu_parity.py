@@ -348,3 +348,20 @@ def test_liquid_1m_full_size(lj):
         s.move_particles(x1)
         check_against_oracle(s, sc, x1)
         s.close()
+
+
+@pytest.mark.parametrize("method", ["VL", "LC", "CL", "VLW"])
+def test_smallest_boxes_twenty_seeds(lj, method):
+    """The smallest box the library accepts (L = 2 (r_c + skin)(1 + 2^-10),
+    plus 0.01): two cells per side, every stencil wraps onto the same cells
+    with two images; 20 seeded random gases, pair sets and forces exact."""
+    L = 2 * 2.8 * (1 + 1.0 / 1024) + 0.01
+    kw = dict(method=method, rebuild_interval=10)
+    if method == "CL":
+        kw.update(cluster_size=4, threads_per_unit=4)
+    for seed in range(20):
+        sc = scenarios.random_gas(120, L, seed=100 + seed, min_dist=0.8)
+        s = lj.System(sc)
+        s.set_config(**kw)
+        check_against_oracle(s, sc, sc["x"])
+        s.close()
