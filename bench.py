@@ -507,12 +507,21 @@ def run_ours(args):
         "batch": bat,
         "inhomogeneous": inh,
     }
-    # kernels launched in the timed region: per step the force (and update
-    # when N3L is on) and the control kernel, per rebuild its chain, plus the
-    # per-call loop-init and command kernels
+    # kernels launched in the timed region.  Graph steps: the force (and
+    # update when N3L is on) and the control kernel, the rebuild chain when a
+    # rebuild runs, and the loop-init and command kernels of each call.
+    # Tuning trials run as plain launches: every trial step launches the
+    # whole chain (its kernels return at once unless a rebuild is due), and
+    # each trial first builds its structure.  Chain lengths are the chosen
+    # configuration's (trials of other methods differ by one or two kernels).
     n3 = 1 if chosen.newton3 else 0
     chain = 5 + {lj.METHOD_VL: 1, lj.METHOD_CLUSTER: 2, lj.METHOD_VLW: 2}.get(chosen.method, 0)
-    line["gpu_launches"] = int(steps_done * (2 + n3) + run["rebuilds"] * chain)
+    trial_steps = rep["trial_steps_total"] if rep else 0
+    ntrial = rep["ntrialled"] if rep else 0
+    graph_steps = steps_done - trial_steps
+    graph_rebuilds = max(0, run["rebuilds"] - ntrial - 1)
+    line["gpu_launches"] = int(trial_steps * (chain + 2 + n3) + ntrial * (chain + 3) +
+                               graph_steps * (2 + n3) + graph_rebuilds * chain + 4)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
