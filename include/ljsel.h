@@ -403,6 +403,13 @@ ljsel_status ljsel_batch_profile_steps(ljsel_batch b, int64_t nsteps, ljsel_prof
 ljsel_status ljsel_batch_autotune(ljsel_batch b, int32_t trial_steps, int32_t ncand, const ljsel_batch_tile *cand,
                                   ljsel_batch_tile *chosen, double *costs_ms);
 
+/* Self-test of the failure path of the library's bounded device waits (the
+ * look-back of the cell scan, the window loads): one GPU thread waits on a
+ * flag that nothing sets, gives up after `polls` polls (1 .. 2^24, about
+ * 50 ns each) and records a timeout, which the host reads.  Returns
+ * LJSEL_ERR_TIMEOUT when the path works; the GPU context stays usable.    */
+ljsel_status ljsel_selftest_wait_timeout(int64_t polls);
+
 /* Allocation-free force evaluation.  The paper has no counterpart: this is
  * a service for callers that cannot allocate device memory -- code running
  * while a stream is captured into a CUDA graph, code inside a framework

@@ -132,6 +132,7 @@ _P = ctypes.c_void_p
 _SIGS = {
     "ljsel_last_error": ([], ctypes.c_char_p),
     "ljsel_abi_version": ([], ctypes.c_int32),
+    "ljsel_selftest_wait_timeout": ([ctypes.c_int64], ctypes.c_int),
     "ljsel_create": ([ctypes.POINTER(ljsel_params), ctypes.c_int64, _P, _P, _P, ctypes.c_int32, _P,
                       ctypes.POINTER(_P)], ctypes.c_int),
     "ljsel_destroy": ([_P], ctypes.c_int),
@@ -265,6 +266,11 @@ def ljsel_last_error() -> str:
 
 def ljsel_abi_version() -> int:
     return int(lib().ljsel_abi_version())
+
+
+def ljsel_selftest_wait_timeout(polls=1 << 16):
+    """Runs the bounded-wait failure path on the GPU; returns the status code (LJSEL_ERR_TIMEOUT expected)."""
+    return int(lib().ljsel_selftest_wait_timeout(int(polls)))
 
 
 def ljsel_create(params: ljsel_params, n, pos, vel, types=None, stream=None):
@@ -469,6 +475,7 @@ class System:
         if isinstance(types, np.ndarray):
             types = np.ascontiguousarray(types, np.int32)
         self.n = int(x.shape[0])
+        self.types = None if types is None else (types if isinstance(types, np.ndarray) else types.cpu().numpy())
         self.h = ljsel_create(self.params, self.n, x, v, types, stream)
 
     def close(self):
@@ -538,6 +545,26 @@ class System:
 
     def rebuild(self):
         ljsel_rebuild(self.h)
+
+    def checkpoint(self, path):
+        """Positions (wrapped), integer-step velocities, types, parameters and the
+        configuration to an .npz file; System.from_checkpoint resumes from it."""
+        x, v = self.state()
+        t = np.zeros(self.n, np.int32) if self.types is None else np.asarray(self.types, np.int32)
+        np.savez(path, x=x, v=v, types=t, params=np.frombuffer(bytes(self.params), np.uint8),
+                 config=np.frombuffer(bytes(self.config()), np.uint8))
+
+    @classmethod
+    def from_checkpoint(cls, path, stream=None):
+        z = np.load(path)
+        obj = cls.__new__(cls)
+        obj.params = ljsel_params.from_buffer_copy(z["params"].tobytes())
+        obj.n = int(z["x"].shape[0])
+        obj.types = np.ascontiguousarray(z["types"], np.int32)
+        obj.h = ljsel_create(obj.params, obj.n, np.ascontiguousarray(z["x"]), np.ascontiguousarray(z["v"]),
+                             obj.types, stream)
+        ljsel_set_config(obj.h, ljsel_config.from_buffer_copy(z["config"].tobytes()))
+        return obj
 
     @property
     def ntypes(self):

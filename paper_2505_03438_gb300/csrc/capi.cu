@@ -53,6 +53,13 @@ __global__ void k_bin_counts(const double *X, int n, BinGrid g, int *counts) {
     atomicAdd(&counts[(c[2] * g.nb[1] + c[1]) * g.nb[0] + c[0]], 1);
 }
 
+// Self-test of the bounded device wait: one thread waits on a flag nothing
+// sets, gives up after `polls` polls and records a timeout.
+__global__ void k_selftest_wait(Ctrl *C, const unsigned long long *flag, int polls) {
+    const unsigned long long v = spin_until(flag, ~0ull, polls);
+    if (!v) C->timeout = 1;
+}
+
 ljsel_config default_config(const ljsel_params &p) {
     ljsel_config c{};
     c.method = LJSEL_METHOD_VL;
@@ -99,6 +106,26 @@ std::vector<ljsel_config> default_candidates(const System &s) {
 extern "C" {
 
 const char *ljsel_last_error(void) { return last_error(); }
+
+ljsel_status ljsel_selftest_wait_timeout(int64_t polls) {
+    set_error("");
+    if (polls < 1 || polls > (1 << 24)) { set_error("polls must be in [1, 2^24]"); return LJSEL_ERR_ARG; }
+    void *mem = nullptr;
+    CK(cudaMalloc(&mem, sizeof(Ctrl) + 64));
+    Ctrl *C = (Ctrl *)mem;
+    unsigned long long *flag = (unsigned long long *)((char *)mem + ((sizeof(Ctrl) + 15) & ~(size_t)15));
+    Ctrl h{};
+    cudaError_t e = cudaMemset(mem, 0, sizeof(Ctrl) + 64);
+    if (e == cudaSuccess) {
+        k_selftest_wait<<<1, 1>>>(C, flag, (int)polls);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&h, C, sizeof(Ctrl), cudaMemcpyDeviceToHost);
+    cudaFree(mem);
+    if (e != cudaSuccess) { set_error(std::string("self-test failed: ") + cudaGetErrorString(e)); return LJSEL_ERR_CUDA; }
+    if (h.timeout) { set_error("a bounded device wait gave up (self-test: nothing sets the flag)"); return LJSEL_ERR_TIMEOUT; }
+    return LJSEL_OK;
+}
 int32_t ljsel_abi_version(void) { return LJSEL_ABI_VERSION; }
 
 ljsel_status ljsel_create(const ljsel_params *params, int64_t n, const double *pos, const double *vel,

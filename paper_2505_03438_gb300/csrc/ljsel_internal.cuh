@@ -202,6 +202,20 @@ static __device__ __noinline__ bool exact_in_range(float fxi, float fyi, float f
     return r2 < rc2d;
 }
 
+// Bounded spin: poll *p until one of the mask bits is set, at most `limit`
+// polls with a short sleep between them.  Returns the last value read; the
+// caller checks the mask and reports a timeout (never traps).
+__device__ __forceinline__ unsigned long long spin_until(const volatile unsigned long long *p, unsigned long long mask,
+                                                         int limit) {
+    unsigned long long v = 0;
+    for (int it = 0; it <= limit; ++it) {
+        v = *p;
+        if (v & mask) break;
+        __nanosleep(32);
+    }
+    return v;
+}
+
 __device__ __forceinline__ float fast_rcp(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));

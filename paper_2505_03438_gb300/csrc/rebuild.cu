@@ -128,14 +128,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(Dev<R> S, int M, int ntil
                 atomicExch(reinterpret_cast<unsigned long long *>(S.scan_partial) + tile, FLAG_A | agg);
                 int p = tile - 1;
                 while (p >= 0) {
-                    unsigned long long v = 0;
-                    int it = 0;
-                    while (true) {
-                        v = st[p];
-                        if (v & (FLAG_A | FLAG_P)) break;
-                        if (++it > SPIN_LIMIT) break;
-                        __nanosleep(32);
-                    }
+                    const unsigned long long v = spin_until(st + p, FLAG_A | FLAG_P, SPIN_LIMIT);
                     if (!(v & (FLAG_A | FLAG_P))) { C->timeout = 1; break; }
                     excl += v & VAL_MASK;
                     if (v & FLAG_P) break;
