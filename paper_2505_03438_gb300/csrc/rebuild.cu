@@ -221,7 +221,8 @@ __global__ void k_sortgather(Dev<R> S) {
 // stencil cells with r^2 < r_list^2 (working precision), j != i; with N3L
 // only j > i.  For each of the 9 neighbouring (y, z) rows the three stencil
 // cells cx-1, cx, cx+1 are one run of consecutive sorted particles (split
-// only at a periodic x edge), walked four candidates at a time.  The 32
+// only at a periodic x edge), tested four candidates at a time into a
+// 32-bit mask per block of 32 candidates.  The 32
 // lanes of a warp are 32 consecutive sorted particles, so they span two or
 // three cells and share their runs: each load serves the lanes of one cell
 // with a single address, and no lane idles for want of a particle (a warp
@@ -302,29 +303,42 @@ __global__ void __launch_bounds__(VL_BUILD_THREADS) k_vl_build(Dev<R> S) {
                     // does this run contain i itself without an image?
                     const bool self = code == 0 && jb <= ii && ii < je;
                     const R xs = pi.x - (R)sx * S.box[0], ys = pi.y - (R)sy * S.box[1], zs = pi.z - (R)sz * S.box[2];
-                    int j = jb;
-                    for (; j + 4 <= je; j += 4) {
-                        const V4<R> q0 = ldpos(P, j), q1 = ldpos(P, j + 1), q2 = ldpos(P, j + 2), q3 = ldpos(P, j + 3);
-                        bool t0 = r2_of(xs - q0.x, ys - q0.y, zs - q0.z) < S.rlist2;
-                        bool t1 = r2_of(xs - q1.x, ys - q1.y, zs - q1.z) < S.rlist2;
-                        bool t2 = r2_of(xs - q2.x, ys - q2.y, zs - q2.z) < S.rlist2;
-                        bool t3 = r2_of(xs - q3.x, ys - q3.y, zs - q3.z) < S.rlist2;
-                        if (self) {
-                            if (N3L) { t0 = t0 && j > i; t1 = t1 && j + 1 > i; t2 = t2 && j + 2 > i; t3 = t3 && j + 3 > i; }
-                            else { t0 = t0 && j != i; t1 = t1 && j + 1 != i; t2 = t2 && j + 2 != i; t3 = t3 && j + 3 != i; }
+                    // candidates in blocks of 32: the tests fill a bit mask, then
+                    // only the accepted bits are appended (the append path runs
+                    // once per entry, not once per candidate, so lanes of a warp
+                    // diverge far less)
+                    for (int j0 = jb; j0 < je; j0 += 32) {
+                        const int m = min(32, je - j0);
+                        uint32_t mask = 0;
+                        int t = 0;
+                        for (; t + 4 <= m; t += 4) {
+                            const int j = j0 + t;
+                            const V4<R> q0 = ldpos(P, j), q1 = ldpos(P, j + 1), q2 = ldpos(P, j + 2), q3 = ldpos(P, j + 3);
+                            const uint32_t b = (uint32_t)(r2_of(xs - q0.x, ys - q0.y, zs - q0.z) < S.rlist2) |
+                                               ((uint32_t)(r2_of(xs - q1.x, ys - q1.y, zs - q1.z) < S.rlist2) << 1) |
+                                               ((uint32_t)(r2_of(xs - q2.x, ys - q2.y, zs - q2.z) < S.rlist2) << 2) |
+                                               ((uint32_t)(r2_of(xs - q3.x, ys - q3.y, zs - q3.z) < S.rlist2) << 3);
+                            mask |= b << t;
                         }
-                        if (act && (t0 | t1 | t2 | t3)) {
-                            if (t0) accept(j, code);
-                            if (t1) accept(j + 1, code);
-                            if (t2) accept(j + 2, code);
-                            if (t3) accept(j + 3, code);
+                        for (; t < m; ++t) {
+                            const V4<R> q = ldpos(P, j0 + t);
+                            mask |= (uint32_t)(r2_of(xs - q.x, ys - q.y, zs - q.z) < S.rlist2) << t;
                         }
-                    }
-                    for (; j < je; ++j) {
-                        const V4<R> q = ldpos(P, j);
-                        bool t = r2_of(xs - q.x, ys - q.y, zs - q.z) < S.rlist2;
-                        if (self) t = t && (N3L ? j > i : j != i);
-                        if (act && t) accept(j, code);
+                        if (self) {  // drop j == i, and with N3L every j <= i
+                            const int rel = ii - j0;
+                            if (N3L) {
+                                if (rel >= 31) mask = 0;
+                                else if (rel >= 0) mask &= ~((2u << rel) - 1u);
+                            } else if (rel >= 0 && rel < 32) {
+                                mask &= ~(1u << rel);
+                            }
+                        }
+                        if (!act) mask = 0;
+                        while (mask) {
+                            const int b = __ffs(mask) - 1;
+                            mask &= mask - 1;
+                            accept(j0 + b, code);
+                        }
                     }
                 }
             }
