@@ -223,7 +223,20 @@ ljsel_status ljsel_set_config(ljsel_system h, const ljsel_config *cfg) {
     TRY(validate_config(*s, cfg));
     ljsel_config c = *cfg;
     if (c.method != LJSEL_METHOD_CLUSTER) c.cluster_size = 1;
+    const ljsel_config old = s->cfg;
     s->cfg = c;
+    // with N3L the force buffer accumulates and must start at zero; without
+    // it a force evaluation leaves its result there
+    if (c.newton3 && !old.newton3) {
+        TRY(dispatch(s, [&](auto z) -> ljsel_status {
+            using R = decltype(z);
+            Dev<R> S;
+            s->fill_dev(S);
+            launch_zero_force(S, s->stream);
+            CK(cudaGetLastError());
+            return LJSEL_OK;
+        }));
+    }
     return s->apply_config();
 }
 
