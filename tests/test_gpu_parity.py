@@ -365,3 +365,21 @@ def test_smallest_boxes_twenty_seeds(lj, method):
         s.set_config(**kw)
         check_against_oracle(s, sc, sc["x"])
         s.close()
+
+
+@pytest.mark.parametrize("n3l_cfg", [dict(method="VL", newton3=True), dict(method="LC", newton3=True),
+                                     dict(method="CL", cluster_size=4, newton3=True, threads_per_unit=4)],
+                         ids=["VL", "LC", "CL4"])
+def test_switch_to_newton3_after_a_force_evaluation(lj, n3l_cfg):
+    """A force evaluation without N3L leaves its forces in the buffer that N3L
+    kernels accumulate into; switching to an N3L configuration must not
+    carry them into the next steps (FP64 path on the oracle's trajectory)."""
+    sc = scenarios.fcc_liquid(5, seed=17, jitter=0.1)
+    s = lj.System(sc, precision=1)
+    s.compute()
+    s.set_config(rebuild_interval=10, **n3l_cfg)
+    s.step(10)
+    x, v = s.state()
+    xo, vo, *_ = oracle.verlet_run(sc["x"], sc["v"], None, [1.0], _orc_params(sc), sc["dt"], 10)
+    assert np.abs(_wrapdiff(x, xo, sc["box"][0])).max() < 1e-10
+    assert np.abs(v - vo).max() < 1e-10
