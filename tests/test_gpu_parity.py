@@ -383,3 +383,22 @@ def test_switch_to_newton3_after_a_force_evaluation(lj, n3l_cfg):
     xo, vo, *_ = oracle.verlet_run(sc["x"], sc["v"], None, [1.0], _orc_params(sc), sc["dt"], 10)
     assert np.abs(_wrapdiff(x, xo, sc["box"][0])).max() < 1e-10
     assert np.abs(v - vo).max() < 1e-10
+
+
+def test_unshifted_potential_and_unequal_masses_fp64(lj):
+    """Energy without the shift at r_c, and a binary mixture whose species
+    have masses 1 and 2: the FP64 trajectory is the oracle's."""
+    sc = dict(scenarios.binary_mixture(seed=15, nside=9), shift=False, mass=np.array([1.0, 2.0]))
+    p = oracle.make_params(sc["box"], sc["eps"], sc["sigma"], sc["rcut"], False)
+    s = lj.System(sc, precision=1)
+    F, e, w = s.compute()
+    ref = oracle.forces_cells(sc["x"], sc["types"], p)
+    assert np.abs(F - ref["F"]).max() < 1e-11 * np.abs(ref["F"]).max()
+    assert abs(e - ref["U"]) < 1e-11 * abs(ref["U"]) and abs(w - ref["W"]) < 1e-11 * abs(ref["W"])
+    s.step(40)
+    x, v = s.state()
+    xo, vo, epo, eko, _ = oracle.verlet_run(sc["x"], sc["v"], sc["types"], sc["mass"], p, sc["dt"], 40)
+    assert np.abs(_wrapdiff(x, xo, sc["box"][0])).max() < 1e-10
+    assert np.abs(v - vo).max() < 1e-10
+    ep, ek, _ = s.energy()
+    assert abs(ep - epo[-1]) < 1e-9 * abs(epo[-1]) and abs(ek - eko[-1]) < 1e-9 * abs(eko[-1])
