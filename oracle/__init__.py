@@ -50,6 +50,7 @@ class Params(ctypes.Structure):
         ("eps", ctypes.c_double * (MAX_TYPES * MAX_TYPES)),
         ("sigma", ctypes.c_double * (MAX_TYPES * MAX_TYPES)),
         ("rcut", ctypes.c_double * (MAX_TYPES * MAX_TYPES)),
+        ("walls", ctypes.c_int32 * 3),
     ]
 
 
@@ -84,6 +85,9 @@ def _bind(lib):
     lib.orc_rollout_vjp.argtypes = [ctypes.c_int64, _D, _D, _I32, _D, ctypes.POINTER(Params), ctypes.c_double,
                                     ctypes.c_int64, _D, _D, _D, _D, _D, _D]
     lib.orc_rollout_vjp.restype = None
+    lib.orc_thermostat.argtypes = [ctypes.c_int64, _D, _I32, _D, ctypes.POINTER(Params), ctypes.c_double,
+                                   ctypes.c_double]
+    lib.orc_thermostat.restype = ctypes.c_double
     return lib
 
 
@@ -106,8 +110,9 @@ def _ip(a):
     return a.ctypes.data_as(_I32)
 
 
-def make_params(box, eps, sigma, rcut, shift=True) -> Params:
-    """Pack a parameter set.  eps/sigma/rcut: scalars (one type) or ntypes x ntypes."""
+def make_params(box, eps, sigma, rcut, shift=True, walls=(0, 0, 0)) -> Params:
+    """Pack a parameter set.  eps/sigma/rcut: scalars (one type) or ntypes x ntypes;
+    walls[d] = 1 closes dimension d with reflective walls (no periodic image)."""
     eps = np.atleast_2d(np.asarray(eps, dtype=np.float64))
     sigma = np.atleast_2d(np.asarray(sigma, dtype=np.float64))
     nt = eps.shape[0]
@@ -120,6 +125,8 @@ def make_params(box, eps, sigma, rcut, shift=True) -> Params:
         p.box[d] = float(box[d])
     p.ntypes = nt
     p.shift = 1 if shift else 0
+    for d in range(3):
+        p.walls[d] = 1 if walls[d] else 0
     for a in range(nt):
         for b in range(nt):
             p.eps[a * nt + b] = float(eps[a, b])
@@ -356,3 +363,15 @@ def rollout_loss_grad(x0, v0, types, mass, params: Params, dt, nsteps, Fstar_end
     L, gxN, ge1, gs1 = force_loss_grad(xs[nsteps], types, params, Fstar_end, lib=lib)
     gx0, gv0, ge2, gs2 = rollout_vjp(x0, v0, types, mass, params, dt, nsteps, gxN, np.zeros_like(gxN), lib=lib)
     return L, gx0, gv0, ge1 + ge2, gs1 + gs2
+
+
+def thermostat(v, types, mass, params: Params, target, max_change, lib=None):
+    """Velocity scaling towards the target temperature by at most max_change
+    (walled heating sphere, Sec. 6).  Returns (scaled v, T before)."""
+    lib = lib or load()
+    v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1, 3).copy()
+    n = v.shape[0]
+    types = np.zeros(n, np.int32) if types is None else np.ascontiguousarray(types, np.int32)
+    mass = np.ascontiguousarray(np.atleast_1d(np.asarray(mass, np.float64)))
+    T = lib.orc_thermostat(n, _dp(v), _ip(types), _dp(mass), ctypes.byref(params), float(target), float(max_change))
+    return v, T

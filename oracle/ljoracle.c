@@ -25,7 +25,11 @@
  *     multiply-add, where dx = x_i - (x_j + k*L) and k in {-1,0,1} is the
  *     minimum image;
  *   - Stormer-Verlet in velocity (kick-drift-kick) form, positions wrapped
- *     into [0, L) after every drift.
+ *     into [0, L) after every drift;
+ *   - a dimension may instead be closed by reflective walls at 0 and L (the
+ *     walled heating-sphere conditions of Sec. 6): no periodic image in it,
+ *     and a particle that crosses a wall after a drift is mirrored back with
+ *     its velocity component reversed.
  *
  * Compile with -O2 -ffp-contract=off (the build script does).  "Parity
  * unpinned" applies to nothing in this file: every routine is pinned by the
@@ -49,6 +53,7 @@ typedef struct orc_params {
     double eps[ORC_MAX_TYPES * ORC_MAX_TYPES];  /* row-major, symmetric      */
     double sigma[ORC_MAX_TYPES * ORC_MAX_TYPES];
     double rcut[ORC_MAX_TYPES * ORC_MAX_TYPES];
+    int32_t walls[3];                           /* 1: reflective walls in d  */
 } orc_params;
 
 /* ---------------------------------------------------------------------- */
@@ -89,6 +94,13 @@ static int min_image_k(double xi, double xj, double L)
     if (d > 0.5 * L) return 1;
     if (d < -0.5 * L) return -1;
     return 0;
+}
+
+/* Image coefficient of dimension d: the minimum image in a periodic
+ * dimension, none between walls.                                          */
+static int image_k(const orc_params *p, int d, double xi, double xj)
+{
+    return p->walls[d] ? 0 : min_image_k(xi, xj, p->box[d]);
 }
 
 /* The defining arithmetic of a displacement component and of r^2.        */
@@ -137,9 +149,9 @@ int64_t orc_forces_brute(int64_t n, const double *x, const int32_t *type,
     for (int64_t i = 0; i < n; ++i) {
         for (int64_t j = i + 1; j < n; ++j) {
             int t = type[i] * nt + type[j];
-            double dx = image_dx(x[3*i+0], x[3*j+0], p->box[0], min_image_k(x[3*i+0], x[3*j+0], p->box[0]));
-            double dy = image_dx(x[3*i+1], x[3*j+1], p->box[1], min_image_k(x[3*i+1], x[3*j+1], p->box[1]));
-            double dz = image_dx(x[3*i+2], x[3*j+2], p->box[2], min_image_k(x[3*i+2], x[3*j+2], p->box[2]));
+            double dx = image_dx(x[3*i+0], x[3*j+0], p->box[0], image_k(p, 0, x[3*i+0], x[3*j+0]));
+            double dy = image_dx(x[3*i+1], x[3*j+1], p->box[1], image_k(p, 1, x[3*i+1], x[3*j+1]));
+            double dz = image_dx(x[3*i+2], x[3*j+2], p->box[2], image_k(p, 2, x[3*i+2], x[3*j+2]));
             double r2 = r2_of(dx, dy, dz);
             double rc = p->rcut[t];
             if (!(r2 < rc * rc)) continue;
@@ -203,7 +215,7 @@ int64_t orc_forces_cells(int64_t n, const double *x, const int32_t *type,
     for (int64_t i = n - 1; i >= 0; --i) {
         int64_t c3[3];
         for (int d = 0; d < 3; ++d) {
-            int64_t m = (int64_t)floor(x[3*i+d] / p->box[d]);
+            int64_t m = p->walls[d] ? 0 : (int64_t)floor(x[3*i+d] / p->box[d]);
             double xw = x[3*i+d] - (double)m * p->box[d];
             int64_t c = (int64_t)floor(xw / side[d]);
             if (c < 0) c = 0;
@@ -235,6 +247,7 @@ int64_t orc_forces_cells(int64_t n, const double *x, const int32_t *type,
                 k[d] = floor_div(raw[d], nc[d]);
                 cw[d] = raw[d] - k[d] * nc[d];
                 if (k[d] < -1 || k[d] > 1) skip = 1;
+                if (p->walls[d] && k[d] != 0) skip = 1;  /* no image between walls */
             }
             if (skip) continue;
             /* a cell reached twice with the same image would double count;
@@ -286,6 +299,15 @@ static void wrap_coord(double *x, double L)
     while (*x >= L) *x -= L;
 }
 
+/* Reflective walls at 0 and L: mirror the position back into the box and
+ * reverse the velocity component.                                         */
+static void reflect_coord(double *x, double *v, double L)
+{
+    if (!isfinite(*x)) return;
+    if (*x < 0.0) { *x = -*x; *v = -*v; }
+    else if (*x > L) { *x = 2.0 * L - *x; *v = -*v; }
+}
+
 static double kinetic(int64_t n, const double *v, const int32_t *type, const double *mass)
 {
     double ke = 0.0;
@@ -314,7 +336,8 @@ int32_t orc_verlet_run(int64_t n, double *x, double *v, const int32_t *type,
             for (int d = 0; d < 3; ++d) {
                 v[3*i+d] += h * F[3*i+d];
                 x[3*i+d] += dt * v[3*i+d];
-                wrap_coord(&x[3*i+d], p->box[d]);
+                if (p->walls[d]) reflect_coord(&x[3*i+d], &v[3*i+d], p->box[d]);
+                else wrap_coord(&x[3*i+d], p->box[d]);
             }
         }
         orc_forces_cells(n, x, type, p, cell_min, nthreads, F, &U, &W, NULL, 0);
@@ -421,7 +444,7 @@ static void lj_force_derivs(double s, double eps, double sig, double *g, double 
 static void pair_dx(const double *x, int64_t i, int64_t j, const orc_params *p, double r[3])
 {
     for (int d = 0; d < 3; ++d)
-        r[d] = image_dx(x[3*i+d], x[3*j+d], p->box[d], min_image_k(x[3*i+d], x[3*j+d], p->box[d]));
+        r[d] = image_dx(x[3*i+d], x[3*j+d], p->box[d], image_k(p, d, x[3*i+d], x[3*j+d]));
 }
 
 /* Forces over a given list of unordered pairs (the frozen mask), minimum  *
@@ -599,4 +622,30 @@ void orc_rollout_vjp(int64_t n, const double *x0, const double *v0, const int32_
         }
     }
     free(xs); free(F); free(cot); free(g);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Velocity-scaling thermostat (the heating of the walled sphere, Sec. 6): *
+ * the temperature T = sum m v^2 / dof (dof = 3N - 3 in a periodic box,    *
+ * whose total momentum is conserved; 3N when any dimension has walls) is  *
+ * moved towards the target by at most max_change, by scaling every        *
+ * velocity with sqrt(T_new / T).  Returns T before the scaling.           */
+double orc_thermostat(int64_t n, double *v, const int32_t *type, const double *mass, const orc_params *p,
+                      double target, double max_change)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double m = mass[type[i]];
+        s += m * (v[3*i] * v[3*i] + v[3*i+1] * v[3*i+1] + v[3*i+2] * v[3*i+2]);
+    }
+    int walled = p->walls[0] || p->walls[1] || p->walls[2];
+    double dof = walled ? 3.0 * (double)n : 3.0 * (double)n - 3.0;
+    double T = s / dof;
+    if (!(T > 0.0)) return T;
+    double dT = target - T;
+    if (dT > max_change) dT = max_change;
+    if (dT < -max_change) dT = -max_change;
+    double f = sqrt((T + dT) / T);
+    for (int64_t k = 0; k < 3 * n; ++k) v[k] *= f;
+    return T;
 }

@@ -435,7 +435,84 @@ def pin_rollout_symplectic(lib, nsteps=10):
     assert np.array_equal(gx, a[0]) and np.array_equal(gv, a[1]) and not ge.any() and not gs.any()
 
 
+# ---------------------------------------------------------------------------
+# Reflective walls and the velocity-scaling thermostat
+
+
+def pin_walls_free_particle(lib):
+    """A lone particle between walls: straight flight, mirrored at each wall
+    with the velocity component reversed (closed form: fold x0 + v t)."""
+    L, dt, nsteps = 6.0, 0.01, 537
+    x0 = np.array([[1.0, 5.5, 3.0]])
+    v0 = np.array([[1.3, 0.7, -2.9]])
+    p = oracle.make_params(L, 1.0, 1.0, 2.5, True, walls=(1, 1, 1))
+    x, v, *_ = oracle.verlet_run(x0, v0, None, [1.0], p, dt, nsteps, lib=lib)
+    u = x0 + v0 * dt * nsteps
+    k = np.floor(u / L)
+    folded = np.where(k % 2 == 0, u - k * L, (k + 1) * L - u)
+    assert np.abs(x - folded).max() < 1e-9, (x, folded)
+    assert np.allclose(v, np.where(k % 2 == 0, v0, -v0))
+
+
+def pin_walls_pairs_and_forces(lib):
+    """Between walls no pair is taken through a face: the brute-force pair set
+    equals scipy's non-periodic k-d tree, and brute force equals linked cells.
+    With walls in x only, y and z keep their minimum images."""
+    from scipy.spatial import cKDTree
+    rng = np.random.default_rng(21)
+    L = 9.0
+    x = rng.uniform(0.0, L, (300, 3))
+    p = oracle.make_params(L, 1.0, 1.0, 2.5, True, walls=(1, 1, 1))
+    b = oracle.forces_brute(x, None, p, pairs=True, lib=lib)
+    ref = cKDTree(x).query_pairs(2.5, output_type="ndarray")
+    assert np.array_equal(oracle.sorted_pairs(b["pairs"]), oracle.sorted_pairs(ref))
+    c = oracle.forces_cells(x, None, p, pairs=True, lib=lib)
+    assert np.array_equal(oracle.sorted_pairs(c["pairs"]), oracle.sorted_pairs(ref))
+    assert np.abs(b["F"] - c["F"]).max() < 1e-9 * np.abs(b["F"]).max()
+    # mixed: walls in x, periodic y and z: distances use images in y, z only
+    p2 = oracle.make_params(L, 1.0, 1.0, 2.5, True, walls=(1, 0, 0))
+    b2 = oracle.forces_brute(x, None, p2, pairs=True, lib=lib)
+    d = x[:, None, :] - x[None, :, :]
+    d[..., 1:] -= L * np.round(d[..., 1:] / L)
+    r2 = (d * d).sum(-1)
+    iu = np.triu_indices(len(x), 1)
+    want = np.stack(iu, 1)[r2[iu] < 6.25]
+    assert np.array_equal(oracle.sorted_pairs(b2["pairs"]), oracle.sorted_pairs(want))
+    c2 = oracle.forces_cells(x, None, p2, pairs=True, lib=lib)
+    assert np.array_equal(oracle.sorted_pairs(c2["pairs"]), oracle.sorted_pairs(want))
+
+
+def pin_walls_nve(lib):
+    """Elastic walls conserve the energy of a liquid in a closed box."""
+    x, box = scenarios.fcc_lattice(4, 0.7)
+    L = box[0] + 1.0  # a gap at the walls
+    x = x + 0.5
+    rng = np.random.default_rng(22)
+    v = scenarios.maxwell_boltzmann(len(x), 1.5, 1.0, rng)
+    p = oracle.make_params(L, 1.0, 1.0, 2.5, True, walls=(1, 1, 1))
+    _, _, ep, ek, _ = oracle.verlet_run(x, v, None, [1.0], p, 0.002, 300, lib=lib)
+    e = ep + ek
+    assert np.abs(e - e[0]).max() < 2e-3 * abs(ek[0]), np.abs(e - e[0]).max()
+
+
+def pin_thermostat(lib):
+    """One scaling step reaches the target within the allowed change, or
+    moves exactly by the allowed change; dof 3N between walls, 3N - 3 in a
+    periodic box."""
+    rng = np.random.default_rng(23)
+    v = rng.normal(0.0, 1.0, (500, 3))
+    for walls, dof in (((0, 0, 0), 1497), ((1, 1, 1), 1500)):
+        p = oracle.make_params(10.0, 1.0, 1.0, 2.5, True, walls=walls)
+        t0 = (v * v).sum() / dof
+        v1, tb = oracle.thermostat(v, None, [1.0], p, t0 + 0.05, 0.1, lib=lib)
+        assert abs(tb - t0) < 1e-12 * t0 and abs((v1 * v1).sum() / dof - (t0 + 0.05)) < 1e-12
+        v2, _ = oracle.thermostat(v, None, [1.0], p, t0 + 5.0, 0.1, lib=lib)
+        assert abs((v2 * v2).sum() / dof - (t0 + 0.1)) < 1e-12
+        assert np.allclose(v2 / v, v2[0, 0] / v[0, 0])  # one common factor
+
+
 ALL_PINS = [pin_lj_minimum, pin_lj_shift, pin_lj_scaling_and_gradient, pin_two_body, pin_fcc_lattice,
             pin_newton3, pin_virial, pin_traversals_agree, pin_drifted_positions, pin_nve,
             pin_reversibility, pin_bin_stats, pin_vjp_two_body, pin_vjp_invariants,
-            pin_vjp_finite_difference, pin_rollout_finite_difference, pin_rollout_symplectic]
+            pin_vjp_finite_difference, pin_rollout_finite_difference, pin_rollout_symplectic,
+            pin_walls_free_particle, pin_walls_pairs_and_forces, pin_walls_nve, pin_thermostat]

@@ -45,6 +45,12 @@ MUTANTS = {
                            "x[3*i+d] += 0.5 * dt * v[3*i+d];\n            }\n    }\n    free(x); free(v); free(F);"),
     "rollout_vjp_drift_coefficient": ("gv0[k] += dt * gx0[k];", "gv0[k] += 0.5 * dt * gx0[k];"),
     "rollout_vjp_kick_levels_swapped": ("xs + (size_t)(t + level) * n3", "xs + (size_t)(t + 1 - level) * n3"),
+    "walls_no_velocity_flip": ("if (*x < 0.0) { *x = -*x; *v = -*v; }", "if (*x < 0.0) { *x = -*x; }"),
+    "walls_far_face_mirror": ("else if (*x > L) { *x = 2.0 * L - *x; *v = -*v; }", "else if (*x > L) { *x = L - *x; *v = -*v; }"),
+    "walls_image_taken": ("return p->walls[d] ? 0 : min_image_k(xi, xj, p->box[d]);", "return min_image_k(xi, xj, p->box[d]);"),
+    "walls_cells_image_taken": ("if (p->walls[d] && k[d] != 0) skip = 1;", "if (0) skip = 1;"),
+    "thermostat_no_sqrt": ("double f = sqrt((T + dT) / T);", "double f = (T + dT) / T;"),
+    "thermostat_dof": ("double dof = walled ? 3.0 * (double)n : 3.0 * (double)n - 3.0;", "double dof = 3.0 * (double)n;"),
     "rollout_vjp_full_kick": ("cot[3*i+d] = 0.5 * dt / mass[type[i]] * gv0[3*i+d];", "cot[3*i+d] = dt / mass[type[i]] * gv0[3*i+d];"),
 }
 
