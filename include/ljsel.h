@@ -84,6 +84,14 @@ typedef struct ljsel_params {
     int32_t use_graphs;        /* 1: ljsel_step runs as one CUDA graph with
                                   device-side rebuild decisions; 0: plain
                                   stream launches                             */
+    int32_t walls[3];          /* 1: dimension d is closed by reflective walls
+                                  at 0 and box[d] (no periodic image; a
+                                  particle crossing a wall is mirrored back
+                                  with its velocity component reversed, the
+                                  walled heating sphere of Sec. 6); 0:
+                                  periodic.  Walls are available with the
+                                  LC and VL methods of single systems.        */
+    int32_t pad;
 } ljsel_params;
 
 /* One algorithmic configuration (the GPU counterpart of a container /
@@ -290,6 +298,14 @@ ljsel_status ljsel_profile_steps(ljsel_system s, int64_t nsteps, ljsel_profile *
 /* The default candidate set for this system: writes up to cap configs and
  * returns their number in *count.                                         */
 ljsel_status ljsel_default_candidates(ljsel_system s, int32_t cap, ljsel_config *out, int32_t *count);
+
+/* Velocity-scaling thermostat (the heating of the walled sphere, Sec. 6):
+ * the temperature T = sum m v^2 / dof of the integer-step velocities (dof =
+ * 3N - 3 in a periodic box, whose total momentum is conserved; 3N when any
+ * dimension has walls) is moved towards `target` by at most `max_change`,
+ * by scaling every velocity with sqrt(T_new / T).  t_before (optional)
+ * receives T before the scaling.  Synchronizes the stream.                */
+ljsel_status ljsel_thermostat(ljsel_system s, double target, double max_change, double *t_before);
 
 /* ---- Gradients --------------------------------------------------------
  * The paper has no gradient; these calls serve the differentiable binary

@@ -47,6 +47,8 @@ class ljsel_params(ctypes.Structure):
         ("dt", ctypes.c_double),
         ("precision", ctypes.c_int32),
         ("use_graphs", ctypes.c_int32),
+        ("walls", ctypes.c_int32 * 3),
+        ("pad", ctypes.c_int32),
     ]
 
 
@@ -142,6 +144,7 @@ _SIGS = {
     "ljsel_compute": ([_P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
                       ctypes.c_int),
     "ljsel_step": ([_P, ctypes.c_int64], ctypes.c_int),
+    "ljsel_thermostat": ([_P, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "ljsel_get_state": ([_P, _P, _P, ctypes.c_int32], ctypes.c_int),
     "ljsel_set_state": ([_P, _P, _P, ctypes.c_int32], ctypes.c_int),
     "ljsel_get_work_positions": ([_P, _P, ctypes.c_int32], ctypes.c_int),
@@ -219,7 +222,7 @@ def _ptr(a):
 
 
 def make_params(box, eps=1.0, sigma=1.0, rcut=2.5, mass=1.0, skin=0.3, dt=0.005, shift=True, precision=0,
-                use_graphs=True) -> ljsel_params:
+                use_graphs=True, walls=(0, 0, 0)) -> ljsel_params:
     eps = np.atleast_2d(np.asarray(eps, np.float64))
     sigma = np.atleast_2d(np.asarray(sigma, np.float64))
     nt = eps.shape[0]
@@ -243,6 +246,8 @@ def make_params(box, eps=1.0, sigma=1.0, rcut=2.5, mass=1.0, skin=0.3, dt=0.005,
     p.dt = float(dt)
     p.precision = int(precision)
     p.use_graphs = 1 if use_graphs else 0
+    for d in range(3):
+        p.walls[d] = 1 if walls[d] else 0
     return p
 
 
@@ -312,6 +317,13 @@ def ljsel_compute(h, forces=None):
 
 def ljsel_step(h, nsteps):
     _check(lib().ljsel_step(h, int(nsteps)))
+
+
+def ljsel_thermostat(h, target, max_change):
+    """Velocity scaling towards `target` by at most `max_change`; returns T before."""
+    t = ctypes.c_double()
+    _check(lib().ljsel_thermostat(h, float(target), float(max_change), ctypes.byref(t)))
+    return t.value
 
 
 def ljsel_get_state(h, pos=None, vel=None):
@@ -462,14 +474,15 @@ class System:
     """Owner of one ljsel handle (destroyed with the object); marshalling only."""
 
     def __init__(self, scenario=None, *, x=None, v=None, types=None, box=None, eps=None, sigma=None, rcut=None,
-                 mass=None, skin=None, dt=None, shift=None, precision=0, use_graphs=True, stream=None):
+                 mass=None, skin=None, dt=None, shift=None, precision=0, use_graphs=True, stream=None, walls=None):
         sc = dict(scenario or {})
         pick = lambda val, key, default: val if val is not None else sc.get(key, default)
         x, v, types = pick(x, "x", None), pick(v, "v", None), pick(types, "types", None)
         box = pick(box, "box", None)
         self.params = make_params(box, pick(eps, "eps", 1.0), pick(sigma, "sigma", 1.0), pick(rcut, "rcut", 2.5),
                                   pick(mass, "mass", 1.0), pick(skin, "skin", 0.3), pick(dt, "dt", 0.005),
-                                  pick(shift, "shift", True), precision, use_graphs)
+                                  pick(shift, "shift", True), precision, use_graphs,
+                                  pick(walls, "walls", (0, 0, 0)))
         x = np.ascontiguousarray(x, np.float64) if isinstance(x, np.ndarray) else x
         v = np.ascontiguousarray(v, np.float64) if isinstance(v, np.ndarray) else v
         if isinstance(types, np.ndarray):
@@ -503,6 +516,9 @@ class System:
 
     def step(self, nsteps):
         ljsel_step(self.h, nsteps)
+
+    def thermostat(self, target, max_change):
+        return ljsel_thermostat(self.h, target, max_change)
 
     def state(self):
         x = np.zeros((self.n, 3))

@@ -116,13 +116,13 @@ __global__ void __launch_bounds__(VJP_THREADS) k_vjp(Dev<R> S, const V4<R> *cot,
         const int rch = S.reach;
         for (int oz = -rch; oz <= rch; ++oz) {
             int wz, sz;
-            if (!wrap_cell(cz, oz, S.nc[2], wz, sz)) continue;
+            if (!stencil_cell(cz, oz, S.nc[2], S.walls[2], wz, sz)) continue;
             for (int oy = -rch; oy <= rch; ++oy) {
                 int wy, sy;
-                if (!wrap_cell(cy, oy, S.nc[1], wy, sy)) continue;
+                if (!stencil_cell(cy, oy, S.nc[1], S.walls[1], wy, sy)) continue;
                 for (int ox = -rch; ox <= rch; ++ox) {
                     int wx, sx;
-                    if (!wrap_cell(cx, ox, S.nc[0], wx, sx)) continue;
+                    if (!stencil_cell(cx, ox, S.nc[0], S.walls[0], wx, sx)) continue;
                     const int cc = (wz * S.nc[1] + wy) * S.nc[0] + wx;
                     const bool img = (sx | sy | sz) != 0;
                     const int jb = S.cell_start[cc], je = S.cell_start[cc + 1];

@@ -860,6 +860,10 @@ ljsel_status ljsel_batch_create(const ljsel_params *params, int32_t nrep, const 
     *out = nullptr;
     if (!params || nrep < 1 || !boxes || !counts) { set_error("params, nrep >= 1, boxes and counts are required"); return LJSEL_ERR_ARG; }
     if (params->ntypes != 1) { set_error("batched replicas hold a single species (ntypes = 1)"); return LJSEL_ERR_UNSUPPORTED; }
+    if (params->walls[0] || params->walls[1] || params->walls[2]) {
+        set_error("batched replicas are periodic");
+        return LJSEL_ERR_UNSUPPORTED;
+    }
     long long ntot = 0;
     for (int r = 0; r < nrep; ++r) {
         if (counts[r] < 0) { set_error("replica counts must be >= 0"); return LJSEL_ERR_ARG; }

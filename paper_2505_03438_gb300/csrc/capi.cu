@@ -60,6 +60,15 @@ __global__ void k_selftest_wait(Ctrl *C, const unsigned long long *flag, int pol
     if (!v) C->timeout = 1;
 }
 
+template <typename R> __global__ void k_scale_velocities(Dev<R> S, double f) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S.n) return;
+    const int sp = S.ctrl->state_par, n = S.n;
+    S.v[sp][i] *= f;
+    S.v[sp][n + i] *= f;
+    S.v[sp][2 * n + i] *= f;
+}
+
 ljsel_config default_config(const ljsel_params &p) {
     ljsel_config c{};
     c.method = LJSEL_METHOD_VL;
@@ -277,6 +286,33 @@ ljsel_status ljsel_compute(ljsel_system h, double *forces, int32_t on_device, do
         TRY(s->check_device_errors());
         if (energy) *energy = s->h_ctrl->epot;
         if (virial) *virial = s->h_ctrl->virial;
+        return LJSEL_OK;
+    });
+}
+
+ljsel_status ljsel_thermostat(ljsel_system h, double target, double max_change, double *t_before) {
+    System *s = (System *)h;
+    if (!s) { set_error("NULL handle"); return LJSEL_ERR_ARG; }
+    if (!(target > 0) || !(max_change >= 0)) { set_error("target > 0 and max_change >= 0 required"); return LJSEL_ERR_ARG; }
+    return dispatch(s, [&](auto z) -> ljsel_status {
+        using R = decltype(z);
+        TRY(s->sync_velocities<R>());
+        Dev<R> S;
+        s->fill_dev(S);
+        TRY(s->cmd(CMD_RESET_EV, 0));
+        launch_kinetic(S, s->stream);
+        CK(cudaGetLastError());
+        TRY(s->read_ctrl());
+        const bool walled = s->params.walls[0] || s->params.walls[1] || s->params.walls[2];
+        const double dof = walled ? 3.0 * s->n : 3.0 * s->n - 3.0;
+        const double T = 2.0 * s->h_ctrl->ekin / dof;
+        if (t_before) *t_before = T;
+        if (!(T > 0)) return LJSEL_OK;
+        double dT = target - T;
+        dT = std::max(-max_change, std::min(max_change, dT));
+        k_scale_velocities<R><<<div_up(s->n, 256), 256, 0, s->stream>>>(S, std::sqrt((T + dT) / T));
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(s->stream));
         return LJSEL_OK;
     });
 }

@@ -127,6 +127,10 @@ __device__ __forceinline__ void integrate_one(const Dev<R> &S, int sp, int pp, i
     double x = fma(dt, vx, X[i]);
     double y = fma(dt, vy, X[n + i]);
     double z = fma(dt, vz, X[2 * n + i]);
+    // reflective walls: mirror a crossing back and reverse the velocity component
+    if (S.walls[0]) { if (x < 0.0) { x = -x; vx = -vx; } else if (x > S.boxd[0]) { x = 2.0 * S.boxd[0] - x; vx = -vx; } }
+    if (S.walls[1]) { if (y < 0.0) { y = -y; vy = -vy; } else if (y > S.boxd[1]) { y = 2.0 * S.boxd[1] - y; vy = -vy; } }
+    if (S.walls[2]) { if (z < 0.0) { z = -z; vz = -vz; } else if (z > S.boxd[2]) { z = 2.0 * S.boxd[2] - z; vz = -vz; } }
     V[i] = vx; V[n + i] = vy; V[2 * n + i] = vz;
     X[i] = x; X[n + i] = y; X[2 * n + i] = z;
     V4<R> w = make_pos((R)x, (R)y, (R)z, t);
@@ -286,13 +290,13 @@ __global__ void __launch_bounds__(FORCE_THREADS) k_lc(Dev<R> S, int2 *pairs, lon
         const int rch = S.reach;
         for (int oz = -rch; oz <= rch; ++oz) {
             int wz, sz;
-            if (!wrap_cell(cz, oz, S.nc[2], wz, sz)) continue;
+            if (!stencil_cell(cz, oz, S.nc[2], S.walls[2], wz, sz)) continue;
             for (int oy = -rch; oy <= rch; ++oy) {
                 int wy, sy;
-                if (!wrap_cell(cy, oy, S.nc[1], wy, sy)) continue;
+                if (!stencil_cell(cy, oy, S.nc[1], S.walls[1], wy, sy)) continue;
                 for (int ox = -rch; ox <= rch; ++ox) {
                     int wx, sx;
-                    if (!wrap_cell(cx, ox, S.nc[0], wx, sx)) continue;
+                    if (!stencil_cell(cx, ox, S.nc[0], S.walls[0], wx, sx)) continue;
                     const int cc = (wz * S.nc[1] + wy) * S.nc[0] + wx;
                     const bool img = (sx | sy | sz) != 0;
                     const int jb = S.cell_start[cc], je = S.cell_start[cc + 1];
@@ -412,7 +416,7 @@ __global__ void k_export_state(Dev<R> S, double *pos, double *vel, int wrap) {
     for (int d = 0; d < 3; ++d) {
         if (pos) {
             double x = S.x[sp][d * n + i];
-            if (wrap) {
+            if (wrap && !S.walls[d]) {
                 double L = S.boxd[d];
                 if (x < 0.0) x += L;
                 if (x >= L) x -= L;

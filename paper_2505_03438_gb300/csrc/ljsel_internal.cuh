@@ -38,6 +38,16 @@ __host__ __device__ inline bool wrap_cell(int c, int o, int n, int &w, int &s) {
     else if (w >= n) { w -= n; s = 1; }
     return w >= 0 && w < n;
 }
+// The same for a dimension that may be closed by walls: between walls there
+// is no image, and a cell beyond the box does not exist (returns false).
+__host__ __device__ inline bool stencil_cell(int c, int o, int n, int wall, int &w, int &s) {
+    if (wall) {
+        w = c + o;
+        s = 0;
+        return w >= 0 && w < n;
+    }
+    return wrap_cell(c, o, n, w, s);
+}
 __host__ __device__ inline void decode_image(uint32_t c, int &sx, int &sy, int &sz) {
     int s = ((int)c + 13) % 27;
     sx = s % 3 - 1;
@@ -115,6 +125,7 @@ template <typename R> struct Dev {
     R box_lo[3];          // FP32 path: box - (float)box, for exact image shifts
     double boxd[3];
     int reach;            // stencil half-width in cells (1 for CSF 1, 2 for CSF 0.5)
+    int walls[3];         // 1: dimension closed by reflective walls
     R rlist2;             // squared list radius (r_c,max + skin, slightly enlarged)
     R half_skin2;         // (skin/2)^2: displacement that forces a rebuild
     // FP64 state, double-buffered by Ctrl::state_par; SoA [3][n]

@@ -193,6 +193,10 @@ extern "C" ljsel_status ljsel_compute_forces_noalloc(const ljsel_params *params,
     ljsel_status st = validate_params(params);
     if (st != LJSEL_OK) return st;
     if (params->precision != 0) { set_error("the allocation-free path computes in FP32 (precision 0)"); return LJSEL_ERR_UNSUPPORTED; }
+    if (params->walls[0] || params->walls[1] || params->walls[2]) {
+        set_error("the allocation-free path handles periodic boxes only");
+        return LJSEL_ERR_UNSUPPORTED;
+    }
     if (!pos || !forces || n < 1) { set_error("pos and forces are required, n >= 1"); return LJSEL_ERR_ARG; }
     if (n > NA_MAX_N) { set_error("n exceeds the allocation-free limit of 131072 particles"); return LJSEL_ERR_CAPACITY; }
     double rcm = 0;

@@ -50,9 +50,11 @@ __global__ void k_bin(Dev<R> S, int ntiles) {
         double L = S.boxd[d];
         double xd = X[d * S.n + p];
         if (!(xd == xd) || fabs(xd) > 4.0 * L) { bad = true; xd = 0.0; }
-        if (xd < 0.0) xd += L;
-        if (xd >= L) xd -= L;
-        if (xd < 0.0 || xd >= L) { xd = xd - L * floor(xd / L); if (xd >= L) xd = 0.0; }
+        if (!S.walls[d]) {  // periodic: wrap (between walls positions stay in [0, L])
+            if (xd < 0.0) xd += L;
+            if (xd >= L) xd -= L;
+            if (xd < 0.0 || xd >= L) { xd = xd - L * floor(xd / L); if (xd >= L) xd = 0.0; }
+        }
         X[d * S.n + p] = xd;
         R w = (R)xd;
         R f = w * S.inv_side[d];
@@ -264,14 +266,14 @@ __global__ void __launch_bounds__(VL_BUILD_THREADS) k_vl_build(Dev<R> S) {
         };
         for (int dz = N3L ? 0 : -1; dz <= 1; ++dz) {
             int wz, sz;
-            wrap_cell(cz, dz, nz, wz, sz);
+            if (!stencil_cell(cz, dz, nz, S.walls[2], wz, sz)) continue;
             for (int dy = -1; dy <= 1; ++dy) {
                 // with N3L a geometric half stencil: rows dz = +1, row (0, +1),
                 // and in i's own row the cells cx (j > i only) and cx + 1
                 if (N3L && dz == 0 && dy < 0) continue;
                 const bool own_row = dz == 0 && dy == 0;
                 int wy, sy;
-                wrap_cell(cy, dy, ny, wy, sy);
+                if (!stencil_cell(cy, dy, ny, S.walls[1], wy, sy)) continue;
                 const int rowc = (wz * ny + wy) * nx;
                 // runs: [left edge][middle][right edge], merged when contiguous
                 for (int seg = 0; seg < 3; ++seg) {
@@ -281,7 +283,7 @@ __global__ void __launch_bounds__(VL_BUILD_THREADS) k_vl_build(Dev<R> S) {
                         if (seg == 1) { xa = xb = cx; sx = 0; }
                         else {
                             int w, s_;
-                            wrap_cell(cx, 1, nx, w, s_);
+                            if (!stencil_cell(cx, 1, nx, S.walls[0], w, s_)) continue;
                             xa = xb = w; sx = s_;
                         }
                     } else if (cx - 1 >= 0 && cx + 1 <= nx - 1) {
@@ -289,13 +291,13 @@ __global__ void __launch_bounds__(VL_BUILD_THREADS) k_vl_build(Dev<R> S) {
                         xa = cx - 1; xb = cx + 1; sx = 0;
                     } else if (seg == 0) {
                         int w, s_;
-                        wrap_cell(cx, -1, nx, w, s_);
+                        if (!stencil_cell(cx, -1, nx, S.walls[0], w, s_)) continue;
                         xa = xb = w; sx = s_;
                     } else if (seg == 1) {
                         xa = xb = cx; sx = 0;
                     } else {
                         int w, s_;
-                        wrap_cell(cx, 1, nx, w, s_);
+                        if (!stencil_cell(cx, 1, nx, S.walls[0], w, s_)) continue;
                         xa = xb = w; sx = s_;
                     }
                     const uint32_t code = encode_image(sx, sy, sz);
@@ -421,13 +423,13 @@ __global__ void k_cp_build(Dev<R> S) {
     int cnt = 0;
     for (int oz = -rch; oz <= rch; ++oz) {
         int wz, sz;
-        if (!wrap_cell(cz, oz, S.nc[2], wz, sz)) continue;
+        if (!stencil_cell(cz, oz, S.nc[2], S.walls[2], wz, sz)) continue;
         for (int oy = -rch; oy <= rch; ++oy) {
             int wy, sy;
-            if (!wrap_cell(cy, oy, S.nc[1], wy, sy)) continue;
+            if (!stencil_cell(cy, oy, S.nc[1], S.walls[1], wy, sy)) continue;
             for (int ox = -rch; ox <= rch; ++ox) {
                 int wx, sx;
-                if (!wrap_cell(cx, ox, S.nc[0], wx, sx)) continue;
+                if (!stencil_cell(cx, ox, S.nc[0], S.walls[0], wx, sx)) continue;
                 int cc = (wz * S.nc[1] + wy) * S.nc[0] + wx;
                 uint32_t code = encode_image(sx, sy, sz);
                 int jb = S.clcell_start[cc], je = S.clcell_start[cc + 1];

@@ -94,7 +94,8 @@ ljsel_status validate_params(const ljsel_params *p) {
     const double rl = rc_max(*p) + p->skin;
     for (int d = 0; d < 3; ++d) {
         if (!(p->box[d] > 0) || !std::isfinite(p->box[d])) { set_error("box lengths must be positive"); return LJSEL_ERR_ARG; }
-        if (p->box[d] < 2.0 * rl * (1.0 + 1.0 / 1024.0)) {
+        if (p->walls[d] != 0 && p->walls[d] != 1) { set_error("walls[d] must be 0 or 1"); return LJSEL_ERR_ARG; }
+        if (!p->walls[d] && p->box[d] < 2.0 * rl * (1.0 + 1.0 / 1024.0)) {
             set_error("box length below 2 (r_c + skin): minimum image would be ambiguous");
             return LJSEL_ERR_BOX;
         }
@@ -121,6 +122,11 @@ ljsel_status validate_config(const System &s, const ljsel_config *c) {
         if (c->csf != 1.0) { set_error("VLW uses csf = 1"); return LJSEL_ERR_UNSUPPORTED; }
     } else {
         if (t != 1) { set_error("LC uses threads_per_unit = 1"); return LJSEL_ERR_UNSUPPORTED; }
+    }
+    const bool walled = s.params.walls[0] || s.params.walls[1] || s.params.walls[2];
+    if (walled && (c->method == LJSEL_METHOD_VLW || c->method == LJSEL_METHOD_CLUSTER)) {
+        set_error("reflective walls are available with the LC and VL methods");
+        return LJSEL_ERR_UNSUPPORTED;
     }
     if (s.params.skin == 0.0 && c->method != LJSEL_METHOD_LC && c->rebuild_interval != 1) {
         set_error("without a skin the lists must be rebuilt every step (R = 1)");
@@ -299,6 +305,7 @@ template <typename R> void System::fill_dev(Dev<R> &S) const {
         S.boxd[d] = params.box[d];
     }
     S.reach = reach;
+    for (int d = 0; d < 3; ++d) S.walls[d] = params.walls[d] ? 1 : 0;
     S.rlist2 = (R)(rlist * rlist);
     const double hs = 0.5 * params.skin;
     S.half_skin2 = (R)(hs * hs);

@@ -93,6 +93,15 @@ def test_invalid_arguments_fail_without_gpu(built):
     with pytest.raises(built.LjselError) as e:
         built.ljsel_batch_create(built.make_params(20.0), boxes, [5, -1], x, x)
     assert e.value.status == 1
+    with pytest.raises(built.LjselError) as e:
+        built.ljsel_batch_create(built.make_params(20.0, walls=(1, 0, 0)), boxes, [2, 2], x, x)
+    assert e.value.status == 9
+    # a wall flag is 0 or 1
+    p = built.make_params(20.0)
+    p.walls[0] = 2
+    with pytest.raises(built.LjselError) as e:
+        built.ljsel_create(p, 4, x, x)
+    assert e.value.status == 1
 
 
 def test_batch_tile_layout(built):
