@@ -355,7 +355,8 @@ def run_ours(args):
         hh = lj.ljsel_create(params, n, x, v, t, stream.cuda_stream)
         if args.method:
             lj.ljsel_set_config(hh, lj.make_config(args.method, cluster_size=args.cluster, newton3=args.newton3,
-                                                   threads_per_unit=args.tpu, rebuild_interval=sc["rebuild"]))
+                                                   threads_per_unit=args.tpu, rebuild_interval=sc["rebuild"],
+                                                   csf=args.csf))
         lj.ljsel_step(hh, W)  # warm-up
         torch.cuda.synchronize()
         return hh
@@ -538,6 +539,7 @@ def main():
     ap.add_argument("--newton3", action="store_true")
     ap.add_argument("--tpu", type=int, default=1)
     ap.add_argument("--cluster", type=int, default=8)
+    ap.add_argument("--csf", type=float, default=1.0, help="with --method: cell size factor (1.0 or 0.5)")
     ap.add_argument("--trial-steps", type=int, default=5)
     ap.add_argument("--probe-steps", type=int, default=2)
     ap.add_argument("--strategy", default="expert", choices=["full", "predictive", "expert"],

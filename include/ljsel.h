@@ -289,6 +289,33 @@ ljsel_status ljsel_get_counters(ljsel_system s, ljsel_counters *c);
 ljsel_status ljsel_autotune(ljsel_system s, const ljsel_tuner_opts *opts,
                             ljsel_config *chosen, ljsel_tuner_report *report);
 
+/* The trial set of one Predictive tuning phase (Sec. 5.1), host only (no
+ * GPU, no handle); ljsel_autotune applies the same rule.  Before phase 2
+ * every configuration that is not blacklisted is trialled.  From phase 2 on,
+ * configuration k is trialled when it is not blacklisted and (a) it has no
+ * measurement, or (b) its predicted cost is at most predict_factor x the
+ * lowest prediction, or (c) it was last trialled retrial_phases or more
+ * phases ago, or (d) it is the incumbent.  The prediction is the line
+ * through its last two measurements evaluated at `phase` (the measurement
+ * itself when there is one), never below half of its last measurement: a
+ * steeply falling pair of costs would otherwise predict a cost near zero
+ * and exclude every other configuration.
+ *   hist_n[k]           0, 1 or 2 measurements of configuration k
+ *   hist_phase, hist_cost [2 k], [2 k + 1]: (phase, cost) of the older and
+ *                       the newer measurement (with one, only [2 k + 1])
+ *   last_trial_phase[k] phase of its last trial (-1: never)
+ *   blacklisted[k]      0 or 1
+ *   incumbent           index of the configuration in use, or -1
+ *   trial[k]            out: 1 if trialled, else 0
+ * All arrays have ncand entries (hist_* 2 ncand) and are host memory.
+ * Errors: LJSEL_ERR_ARG for ncand < 0, a NULL array with ncand > 0, hist_n
+ * outside 0..2, incumbent outside -1..ncand-1 or predict_factor <= 0.     */
+ljsel_status ljsel_predictive_trials(int32_t ncand, int32_t phase, const int32_t *hist_n,
+                                     const int32_t *hist_phase, const double *hist_cost,
+                                     const int32_t *last_trial_phase, const int32_t *blacklisted,
+                                     int32_t incumbent, double predict_factor, int32_t retrial_phases,
+                                     int32_t *trial);
+
 /* Advance nsteps steps with plain stream launches, a CUDA event before and
  * after every kernel class, and report mean GPU times per launch.  The
  * steps advance the simulation like ljsel_step.  Synchronizes every step;

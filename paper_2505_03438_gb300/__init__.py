@@ -181,6 +181,8 @@ _SIGS = {
     "ljsel_batch_profile_steps": ([_P, ctypes.c_int64, ctypes.POINTER(ljsel_profile)], ctypes.c_int),
     "ljsel_batch_autotune": ([_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.POINTER(ljsel_batch_tile), _P],
                              ctypes.c_int),
+    "ljsel_predictive_trials": ([ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.c_int32, ctypes.c_double,
+                                 ctypes.c_int32, _P], ctypes.c_int),
 }
 EXPORTED = tuple(_SIGS)
 _lib = None
@@ -425,6 +427,30 @@ def ljsel_autotune(h, strategy=0, trial_steps=10, predict_factor=2.0, blacklist_
     rep = ljsel_tuner_report()
     _check(lib().ljsel_autotune(h, ctypes.byref(o), ctypes.byref(chosen), ctypes.byref(rep)))
     return chosen, {k: getattr(rep, k) for k, _ in rep._fields_}
+
+
+def ljsel_predictive_trials(phase, history, last_trial_phase, blacklisted, incumbent=-1, predict_factor=2.0,
+                            retrial_phases=4):
+    """Trial set of one Predictive tuning phase (host only).  history[k] is a
+    list of (phase, cost) measurements of configuration k, oldest first (the
+    last two are used).  Returns a list of 0/1 per configuration."""
+    n = len(history)
+    hn = np.zeros(n, np.int32)
+    hp = np.zeros(2 * n, np.int32)
+    hc = np.zeros(2 * n, np.float64)
+    for k, hs in enumerate(history):
+        hs = list(hs)[-2:]
+        hn[k] = len(hs)
+        for q, (ph, c) in enumerate(hs):
+            slot = 2 * k + (1 if len(hs) == 1 else q)
+            hp[slot], hc[slot] = ph, c
+    lt = np.ascontiguousarray(last_trial_phase, np.int32)
+    bl = np.ascontiguousarray(blacklisted, np.int32)
+    out = np.zeros(max(n, 1), np.int32)
+    _check(lib().ljsel_predictive_trials(n, int(phase), hn.ctypes.data, hp.ctypes.data, hc.ctypes.data, lt.ctypes.data,
+                                         bl.ctypes.data, int(incumbent), float(predict_factor), int(retrial_phases),
+                                         out.ctypes.data))
+    return out[:n].tolist()
 
 
 def _table(a, nt):

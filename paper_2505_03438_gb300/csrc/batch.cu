@@ -55,6 +55,7 @@ template <typename R> struct RepInfo {
     R box[3];
     R box_lo[3];  // FP32 path: box - (float)box
     double boxd[3];
+    float box_dn[3];  // largest float <= L: 0 < (float)x < box_dn proves 0 < x < L
     R inv_side[3];
     int nc[3];
     int cell_off;  // first global cell of the replica
@@ -127,13 +128,18 @@ template <typename R> __global__ void k_bbin(BDev<R> S) {
     int c3[3];
     bool bad = false;
     for (int d = 0; d < 3; ++d) {
-        const double L = I.boxd[d];
         double xd = X[d * S.ntot + g];
-        if (!(xd == xd) || fabs(xd) > 4.0 * L) { bad = true; xd = 0.0; }
-        if (xd < 0.0) xd += L;
-        if (xd >= L) xd -= L;
-        if (xd < 0.0 || xd >= L) { xd = xd - L * floor(xd / L); if (xd >= L) xd = 0.0; }
-        X[d * S.ntot + g] = xd;
+        // FP64 arithmetic is scarce: the FP64 wrap only for particles whose
+        // float rounding does not prove 0 < x < L (rounding is monotonic)
+        const float xf = (float)xd;
+        if (!(xf > 0.0f && xf < I.box_dn[d])) {
+            const double L = I.boxd[d];
+            if (!(xd == xd) || fabs(xd) > 4.0 * L) { bad = true; xd = 0.0; }
+            if (xd < 0.0) xd += L;
+            if (xd >= L) xd -= L;
+            if (xd < 0.0 || xd >= L) { xd = xd - L * floor(xd / L); if (xd >= L) xd = 0.0; }
+            X[d * S.ntot + g] = xd;
+        }
         const int c = (int)floor((R)xd * I.inv_side[d]);
         c3[d] = min(max(c, 0), I.nc[d] - 1);
     }
@@ -834,6 +840,9 @@ template <typename R> ljsel_status fill_reps(ljsel_batch_s *b) {
             I.box[d] = (R)L;
             I.box_lo[d] = (R)(L - (double)(R)L);
             I.boxd[d] = L;
+            float lf = (float)L;
+            if ((double)lf > L) lf = std::nextafter(lf, 0.0f);
+            I.box_dn[d] = lf;
             I.inv_side[d] = (R)(I.nc[d] / L);
             nc *= I.nc[d];
         }

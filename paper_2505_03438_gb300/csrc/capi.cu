@@ -101,6 +101,10 @@ std::vector<ljsel_config> default_candidates(const System &s) {
     for (int t : {1, 4}) add(LJSEL_METHOD_VL, 1, 1, t, 1.0, R);
     add(LJSEL_METHOD_VL, 1, 0, 1, 1.0, 2 * R);
     add(LJSEL_METHOD_VL, 1, 0, 2, 1.0, 2 * R);
+    // half-side cells: the list build tests about 40 % of the candidates
+    for (int t : {1, 2, 4}) add(LJSEL_METHOD_VL, 1, 0, t, 0.5, R);
+    add(LJSEL_METHOD_VL, 1, 1, 1, 0.5, R);
+    add(LJSEL_METHOD_VL, 1, 0, 2, 0.5, 2 * R);
     for (int n3 = 0; n3 <= 1; ++n3) add(LJSEL_METHOD_VLW, 1, n3, 1, 1.0, R);
     add(LJSEL_METHOD_VLW, 1, 0, 1, 1.0, 2 * R);
     for (int M : {4, 8, 32}) {
@@ -110,11 +114,62 @@ std::vector<ljsel_config> default_candidates(const System &s) {
     return v;
 }
 
+// Trial set of one Predictive phase (Sec. 5.1); see ljsel_predictive_trials.
+ljsel_status predictive_trials(int32_t ncand, int32_t phase, const int32_t *hist_n, const int32_t *hist_phase,
+                               const double *hist_cost, const int32_t *last_trial_phase, const int32_t *blacklisted,
+                               int32_t incumbent, double predict_factor, int32_t retrial_phases, int32_t *trial) {
+    if (ncand < 0 || incumbent < -1 || incumbent >= ncand || !(predict_factor > 0)) {
+        set_error("invalid argument");
+        return LJSEL_ERR_ARG;
+    }
+    if (ncand > 0 && (!hist_n || !hist_phase || !hist_cost || !last_trial_phase || !blacklisted || !trial)) {
+        set_error("NULL array");
+        return LJSEL_ERR_ARG;
+    }
+    for (int k = 0; k < ncand; ++k)
+        if (hist_n[k] < 0 || hist_n[k] > 2) { set_error("hist_n must be 0, 1 or 2"); return LJSEL_ERR_ARG; }
+    if (phase < 2) {  // the first two phases trial everything
+        for (int k = 0; k < ncand; ++k) trial[k] = blacklisted[k] ? 0 : 1;
+        return LJSEL_OK;
+    }
+    std::vector<double> pred(ncand, -1.0);
+    double best = 1e300;
+    for (int k = 0; k < ncand; ++k) {
+        if (blacklisted[k] || hist_n[k] == 0) continue;
+        const double cb = hist_cost[2 * k + 1];
+        double p = cb;
+        if (hist_n[k] == 2) {
+            const int pa = hist_phase[2 * k], pb = hist_phase[2 * k + 1];
+            const double slope = (cb - hist_cost[2 * k]) / (double)std::max(1, pb - pa);
+            p = std::max(cb + slope * (double)(phase - pb), 0.5 * cb);
+        }
+        pred[k] = p;
+        best = std::min(best, p);
+    }
+    for (int k = 0; k < ncand; ++k) {
+        if (blacklisted[k]) { trial[k] = 0; continue; }
+        const bool unmeasured = pred[k] < 0;
+        const bool near = !unmeasured && pred[k] <= predict_factor * best;
+        const bool stale = phase - last_trial_phase[k] >= std::max(1, retrial_phases);
+        trial[k] = (unmeasured || near || stale || k == incumbent) ? 1 : 0;
+    }
+    return LJSEL_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
 const char *ljsel_last_error(void) { return last_error(); }
+
+ljsel_status ljsel_predictive_trials(int32_t ncand, int32_t phase, const int32_t *hist_n, const int32_t *hist_phase,
+                                     const double *hist_cost, const int32_t *last_trial_phase,
+                                     const int32_t *blacklisted, int32_t incumbent, double predict_factor,
+                                     int32_t retrial_phases, int32_t *trial) {
+    set_error("");
+    return predictive_trials(ncand, phase, hist_n, hist_phase, hist_cost, last_trial_phase, blacklisted, incumbent,
+                             predict_factor, retrial_phases, trial);
+}
 
 ljsel_status ljsel_selftest_wait_timeout(int64_t polls) {
     set_error("");
@@ -686,30 +741,27 @@ ljsel_status ljsel_autotune(ljsel_system h, const ljsel_tuner_opts *opts, ljsel_
         }
         if (!any)
             for (size_t k = 0; k < cands.size(); ++k) trial[k] = !ent[k]->blacklisted;
-    } else if (opts->strategy == 1 && phase >= 2) {
-        std::vector<double> pred(cands.size(), -1.0);
-        double best = 1e300;
-        for (size_t k = 0; k < cands.size(); ++k) {
+    } else if (opts->strategy == 1) {
+        const int nc = (int)cands.size();
+        std::vector<int32_t> hn(nc), hp(2 * nc, 0), lt(nc), bl(nc), tr(nc);
+        std::vector<double> hc(2 * nc, 0.0);
+        int incumbent = -1;
+        for (int k = 0; k < nc; ++k) {
             const auto &hs = ent[k]->history;
-            if (ent[k]->blacklisted || hs.empty()) continue;
-            double p;
-            if (hs.size() == 1) p = hs.back().second;
-            else {
-                const auto &a = hs[hs.size() - 2], &b = hs[hs.size() - 1];
-                double slope = (b.second - a.second) / (double)std::max(1, b.first - a.first);
-                p = b.second + slope * (phase - b.first);
-                if (p < 0.05 * b.second) p = 0.05 * b.second;
+            hn[k] = (int32_t)std::min<size_t>(2, hs.size());
+            for (int q = 0; q < hn[k]; ++q) {
+                const auto &e = hs[hs.size() - hn[k] + q];
+                const int slot = 2 * k + (hn[k] == 1 ? 1 : q);
+                hp[slot] = e.first;
+                hc[slot] = e.second;
             }
-            pred[k] = p;
-            best = std::min(best, p);
+            lt[k] = ent[k]->last_trial_phase;
+            bl[k] = ent[k]->blacklisted ? 1 : 0;
+            if (incumbent < 0 && same_cfg(cands[k], s->cfg)) incumbent = k;
         }
-        for (size_t k = 0; k < cands.size(); ++k) {
-            if (ent[k]->blacklisted) { trial[k] = 0; continue; }
-            if (pred[k] < 0) { trial[k] = 1; continue; }
-            bool near = pred[k] <= opts->predict_factor * best;
-            bool stale = phase - ent[k]->last_trial_phase >= std::max(1, opts->retrial_phases);
-            trial[k] = near || stale;
-        }
+        TRY(predictive_trials(nc, phase, hn.data(), hp.data(), hc.data(), lt.data(), bl.data(), incumbent,
+                              opts->predict_factor, opts->retrial_phases, tr.data()));
+        for (int k = 0; k < nc; ++k) trial[k] = (char)tr[k];
     } else {
         for (size_t k = 0; k < cands.size(); ++k) trial[k] = !ent[k]->blacklisted;
     }

@@ -124,6 +124,7 @@ template <typename R> struct Dev {
     R box[3];
     R box_lo[3];          // FP32 path: box - (float)box, for exact image shifts
     double boxd[3];
+    float box_dn[3];      // largest float <= L: 0 < (float)x < box_dn proves 0 < x < L
     int reach;            // stencil half-width in cells (1 for CSF 1, 2 for CSF 0.5)
     int walls[3];         // 1: dimension closed by reflective walls
     R rlist2;             // squared list radius (r_c,max + skin, slightly enlarged)
@@ -237,6 +238,24 @@ __device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ float r2_of(float dx, float dy, float dz) { return fmaf(dz, dz, fmaf(dy, dy, dx * dx)); }
 __device__ __forceinline__ double r2_of(double dx, double dy, double dz) {
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// Largest required list length of a warp or a block, then one atomicMax on
+// Ctrl::need_cap: same-address atomics serialise in L2, and one per particle
+// (a million per build) cost about as much as the list build itself.
+// Every lane of the warp (every thread of the block) must make the call.
+__device__ __forceinline__ void warp_need_max(Ctrl *C, unsigned v) {
+    const unsigned m = __reduce_max_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(reinterpret_cast<unsigned long long *>(&C->need_cap), (unsigned long long)m);
+}
+__device__ __forceinline__ void block_need_max(Ctrl *C, unsigned v) {
+    __shared__ unsigned s_need;
+    if (threadIdx.x == 0) s_need = 0u;
+    __syncthreads();
+    const unsigned m = __reduce_max_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(&s_need, m);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_need) atomicMax(reinterpret_cast<unsigned long long *>(&C->need_cap), (unsigned long long)s_need);
 }
 
 // Decides "r < r_c" for one pair exactly as the FP64 predicate does: in the

@@ -22,6 +22,7 @@ constexpr unsigned long long FLAG_P = 2ull << 62;  // inclusive prefix published
 constexpr unsigned long long VAL_MASK = (1ull << 62) - 1ull;
 constexpr int SPIN_LIMIT = 1 << 22;
 constexpr int VL_BUILD_THREADS = 128;
+constexpr int VL_BUILD_MIN_BLOCKS = 10;  // 40 warps per SM: at most 48 registers a thread, no spills
 
 __device__ __forceinline__ unsigned morton3(unsigned x, unsigned y, unsigned z) {
     unsigned k = 0;
@@ -40,22 +41,31 @@ __global__ void k_bin(Dev<R> S, int ntiles) {
         C->window_overflow = 0;
         if (S.nstrips) *S.nstrips = 0;
     }
-    if (p >= S.n) return;
+    // every lane stays to the warp-wide match below; lanes past n bin nothing
+    const bool valid = p < S.n;
+    const int pp = valid ? p : 0;
     const int sp = C->state_par;
     double *X = S.x[sp];
     int c3[3];
     unsigned sub[3];
     bool bad = false;
     for (int d = 0; d < 3; ++d) {
-        double L = S.boxd[d];
-        double xd = X[d * S.n + p];
-        if (!(xd == xd) || fabs(xd) > 4.0 * L) { bad = true; xd = 0.0; }
-        if (!S.walls[d]) {  // periodic: wrap (between walls positions stay in [0, L])
-            if (xd < 0.0) xd += L;
-            if (xd >= L) xd -= L;
-            if (xd < 0.0 || xd >= L) { xd = xd - L * floor(xd / L); if (xd >= L) xd = 0.0; }
+        double xd = X[d * S.n + pp];
+        // FP64 arithmetic is scarce on this part: decide "0 < x < L" on the
+        // float rounding (rounding is monotonic, so 0 < (float)x < box_dn
+        // implies it exactly) and take the FP64 path only for the particles
+        // that left the box
+        const float xf = (float)xd;
+        if (!(xf > 0.0f && xf < S.box_dn[d])) {
+            const double L = S.boxd[d];
+            if (!(xd == xd) || fabs(xd) > 4.0 * L) { bad = true; xd = 0.0; }
+            if (!S.walls[d]) {  // periodic: wrap (between walls positions stay in [0, L])
+                if (xd < 0.0) xd += L;
+                if (xd >= L) xd -= L;
+                if (xd < 0.0 || xd >= L) { xd = xd - L * floor(xd / L); if (xd >= L) xd = 0.0; }
+            }
+            if (valid) X[d * S.n + p] = xd;
         }
-        X[d * S.n + p] = xd;
         R w = (R)xd;
         R f = w * S.inv_side[d];
         int c = (int)floor(f);
@@ -64,10 +74,19 @@ __global__ void k_bin(Dev<R> S, int ntiles) {
         sub[d] = (unsigned)(s < 0 ? 0 : (s > 7 ? 7 : s));
         c3[d] = c;
     }
-    if (bad) C->nonfinite = 1;
-    int cell = (c3[2] * S.nc[1] + c3[1]) * S.nc[0] + c3[0];
+    if (bad && valid) C->nonfinite = 1;
+    const int cell = valid ? (c3[2] * S.nc[1] + c3[1]) * S.nc[0] + c3[0] : -1;
+    // slots in the cell: one atomic per distinct cell of the warp (the lanes
+    // of a warp are neighbours from the last sort and share one or two cells)
+    const int lane = threadIdx.x & 31;
+    const unsigned peers = __match_any_sync(0xffffffffu, cell);
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (valid && lane == leader) base = atomicAdd(&S.cell_count[cell], __popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (!valid) return;
     S.cell_of[p] = cell;
-    S.slot_of[p] = atomicAdd(&S.cell_count[cell], 1);
+    S.slot_of[p] = base + __popc(peers & ((1u << lane) - 1u));
     S.key_of[p] = ((unsigned long long)morton3(sub[0], sub[1], sub[2]) << 32) | (unsigned)S.id[sp][p];
 }
 
@@ -168,13 +187,15 @@ __global__ void k_scatter(Dev<R> S) {
     if (!C->rebuild_now) return;
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= S.n) return;
-    int dst = S.cell_start[S.cell_of[p]] + S.slot_of[p];
+    const int cell = S.cell_of[p];
+    const int dst = S.cell_start[cell] + S.slot_of[p];
     S.tmp_idx[dst] = p;
     S.tmp_key[dst] = S.key_of[p];
+    S.cell_sorted[dst] = cell;  // the slot's cell: its final occupant is in the same cell
 }
 
 template <typename R>
-__device__ __forceinline__ void gather_one(const Dev<R> &S, int sp, int pp, int q, int p, int cell) {
+__device__ __forceinline__ void gather_one(const Dev<R> &S, int sp, int pp, int q, int p) {
     const int n = S.n;
     const double *X = S.x[sp];
     const double *V = S.v[sp];
@@ -189,52 +210,44 @@ __device__ __forceinline__ void gather_one(const Dev<R> &S, int sp, int pp, int 
     V4<R> w = make_pos((R)x0, (R)x1, (R)x2, t);
     S.pos[pp][q] = w;
     S.xref[q] = w;
-    S.cell_sorted[q] = cell;
 }
 
-// One warp per cell: rank each element of the cell segment by its key and
-// gather the particle state into its final slot.
+// One thread per slot of the scattered order: the element's rank among the
+// keys of its cell segment is its final place in the cell; the particle
+// state is gathered there.  The lanes of a warp cover one or two cells, so
+// the key reads are shared.
 template <typename R>
 __global__ void k_sortgather(Dev<R> S) {
     Ctrl *C = S.ctrl;
     if (!C->rebuild_now) return;
-    const int lane = threadIdx.x & 31;
-    const int cell = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (cell >= S.ncell) return;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= S.n) return;
     const int sp = C->state_par, pp = C->pos_par;
-    const int start = S.cell_start[cell];
-    const int m = S.cell_start[cell + 1] - start;
-    if (m <= 32) {
-        unsigned long long key = lane < m ? S.tmp_key[start + lane] : ~0ull;
-        int rank = 0;
-        for (int t = 0; t < m; ++t) rank += (__shfl_sync(0xffffffffu, key, t) < key) ? 1 : 0;
-        if (lane < m) gather_one(S, sp, pp, start + rank, S.tmp_idx[start + lane], cell);
-    } else {
-        for (int e = lane; e < m; e += 32) {
-            unsigned long long key = S.tmp_key[start + e];
-            int rank = 0;
-            for (int f = 0; f < m; ++f) rank += (S.tmp_key[start + f] < key) ? 1 : 0;
-            gather_one(S, sp, pp, start + rank, S.tmp_idx[start + e], cell);
-        }
-    }
+    const int cell = S.cell_sorted[e];
+    const int start = S.cell_start[cell], m = S.cell_start[cell + 1] - start;
+    const unsigned long long key = S.tmp_key[e];
+    int rank = 0;
+    for (int f = 0; f < m; ++f) rank += S.tmp_key[start + f] < key ? 1 : 0;
+    gather_one(S, sp, pp, start + rank, S.tmp_idx[e]);
 }
 
-// Verlet-list rows, one thread per sorted particle i: all j in the 27
-// stencil cells with r^2 < r_list^2 (working precision), j != i; with N3L
-// only j > i.  For each of the 9 neighbouring (y, z) rows the three stencil
-// cells cx-1, cx, cx+1 are one run of consecutive sorted particles (split
-// only at a periodic x edge), tested four candidates at a time into a
-// 32-bit mask per block of 32 candidates.  The 32
-// lanes of a warp are 32 consecutive sorted particles, so they span two or
-// three cells and share their runs: each load serves the lanes of one cell
-// with a single address, and no lane idles for want of a particle (a warp
-// per cell would leave about 13 of 32 lanes idle at 19 particles a cell).  Entries without an image go to the front of the
+// Verlet-list rows, one thread per sorted particle i: all j with
+// r^2 < r_list^2 (working precision) in the stencil of (2 RCH + 1)^3 cells
+// (RCH = 1 for CSF 1, 2 for CSF 0.5), j != i; with N3L only the geometric
+// half stencil.  The stencil is walked as (y, z) rows of cells; in each row
+// the x cells cx - RCH .. cx + RCH form one run of consecutive sorted
+// particles, split only at a periodic x edge.  Candidates are tested four at
+// a time into a 32-bit mask per block of 32; only the set bits are appended.
+// The 32 lanes of a warp are 32 consecutive sorted particles and share most
+// of their runs (cutting each particle's runs to the reach of the list
+// radius tests far fewer candidates but makes the lanes' trip counts differ,
+// and measured no faster).  Entries without an image go to the front of the
 // row in 16-byte chunks of four, padded with the sentinel index n; entries
 // with an image go to the back, one by one.  The list test needs no exact
 // image arithmetic: the list radius carries a relative margin of 2^-12, far
 // above the rounding of a plain shift, so i is shifted once per run.
-template <typename R, bool N3L>
-__global__ void __launch_bounds__(VL_BUILD_THREADS) k_vl_build(Dev<R> S) {
+template <typename R, bool N3L, int RCH>
+__global__ void __launch_bounds__(VL_BUILD_THREADS, VL_BUILD_MIN_BLOCKS) k_vl_build(Dev<R> S) {
     Ctrl *C = S.ctrl;
     if (!C->rebuild_now) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -246,121 +259,96 @@ __global__ void __launch_bounds__(VL_BUILD_THREADS) k_vl_build(Dev<R> S) {
     const int cxy = c % (nx * ny);
     const int cx = cxy % nx, cy = cxy / nx, cz = c / (nx * ny);
     const int cap = S.nl_cap;
-    {
-        const V4<R> pi = P[ii];
-        uint32_t *rowp = S.nl + (size_t)ii * cap;
-        uint4 *row = reinterpret_cast<uint4 *>(rowp);
-        uint32_t b0 = 0, b1 = 0, b2 = 0, b3 = 0;
-        int nf = 0, nb = 0;
-        // entries of the current chunk live in a 4-register shift queue and
-        // are stored as one 16-byte chunk when four have been found
-        auto accept = [&](int j, uint32_t code) {
-            if (code == 0) {
-                b3 = b2; b2 = b1; b1 = b0; b0 = (uint32_t)j;
-                ++nf;
-                if ((nf & 3) == 0 && nf + nb <= cap) row[(nf >> 2) - 1] = make_uint4(b0, b1, b2, b3);
-            } else {
-                if (nf + nb < cap && ((nf + 4) & ~3) + nb < cap) rowp[cap - 1 - nb] = (uint32_t)j | (code << JBITS);
-                ++nb;
-            }
-        };
-        for (int dz = N3L ? 0 : -1; dz <= 1; ++dz) {
-            int wz, sz;
-            if (!stencil_cell(cz, dz, nz, S.walls[2], wz, sz)) continue;
-            for (int dy = -1; dy <= 1; ++dy) {
-                // with N3L a geometric half stencil: rows dz = +1, row (0, +1),
-                // and in i's own row the cells cx (j > i only) and cx + 1
-                if (N3L && dz == 0 && dy < 0) continue;
-                const bool own_row = dz == 0 && dy == 0;
-                int wy, sy;
-                if (!stencil_cell(cy, dy, ny, S.walls[1], wy, sy)) continue;
-                const int rowc = (wz * ny + wy) * nx;
-                // runs: [left edge][middle][right edge], merged when contiguous
-                for (int seg = 0; seg < 3; ++seg) {
-                    int xa, xb, sx;  // cells [xa, xb] of this run, image sx
-                    if (N3L && own_row) {
-                        if (seg == 0) continue;  // no cx - 1
-                        if (seg == 1) { xa = xb = cx; sx = 0; }
-                        else {
-                            int w, s_;
-                            if (!stencil_cell(cx, 1, nx, S.walls[0], w, s_)) continue;
-                            xa = xb = w; sx = s_;
-                        }
-                    } else if (cx - 1 >= 0 && cx + 1 <= nx - 1) {
-                        if (seg > 0) break;
-                        xa = cx - 1; xb = cx + 1; sx = 0;
-                    } else if (seg == 0) {
-                        int w, s_;
-                        if (!stencil_cell(cx, -1, nx, S.walls[0], w, s_)) continue;
-                        xa = xb = w; sx = s_;
-                    } else if (seg == 1) {
-                        xa = xb = cx; sx = 0;
-                    } else {
-                        int w, s_;
-                        if (!stencil_cell(cx, 1, nx, S.walls[0], w, s_)) continue;
-                        xa = xb = w; sx = s_;
-                    }
-                    const uint32_t code = encode_image(sx, sy, sz);
-                    int jb = S.cell_start[rowc + xa], je = S.cell_start[rowc + xb + 1];
-                    // does this run contain i itself without an image?
-                    const bool self = code == 0 && jb <= ii && ii < je;
-                    const R xs = pi.x - (R)sx * S.box[0], ys = pi.y - (R)sy * S.box[1], zs = pi.z - (R)sz * S.box[2];
-                    // candidates in blocks of 32: the tests fill a bit mask, then
-                    // only the accepted bits are appended (the append path runs
-                    // once per entry, not once per candidate, so lanes of a warp
-                    // diverge far less)
-                    for (int j0 = jb; j0 < je; j0 += 32) {
-                        const int m = min(32, je - j0);
-                        uint32_t mask = 0;
-                        int t = 0;
-                        for (; t + 4 <= m; t += 4) {
-                            const int j = j0 + t;
-                            const V4<R> q0 = ldpos(P, j), q1 = ldpos(P, j + 1), q2 = ldpos(P, j + 2), q3 = ldpos(P, j + 3);
-                            const uint32_t b = (uint32_t)(r2_of(xs - q0.x, ys - q0.y, zs - q0.z) < S.rlist2) |
-                                               ((uint32_t)(r2_of(xs - q1.x, ys - q1.y, zs - q1.z) < S.rlist2) << 1) |
-                                               ((uint32_t)(r2_of(xs - q2.x, ys - q2.y, zs - q2.z) < S.rlist2) << 2) |
-                                               ((uint32_t)(r2_of(xs - q3.x, ys - q3.y, zs - q3.z) < S.rlist2) << 3);
-                            mask |= b << t;
-                        }
-                        for (; t < m; ++t) {
-                            const V4<R> q = ldpos(P, j0 + t);
-                            mask |= (uint32_t)(r2_of(xs - q.x, ys - q.y, zs - q.z) < S.rlist2) << t;
-                        }
-                        if (self) {  // drop j == i, and with N3L every j <= i
-                            const int rel = ii - j0;
-                            if (N3L) {
-                                if (rel >= 31) mask = 0;
-                                else if (rel >= 0) mask &= ~((2u << rel) - 1u);
-                            } else if (rel >= 0 && rel < 32) {
-                                mask &= ~(1u << rel);
-                            }
-                        }
-                        if (!act) mask = 0;
-                        while (mask) {
-                            const int b = __ffs(mask) - 1;
-                            mask &= mask - 1;
-                            accept(j0 + b, code);
-                        }
-                    }
-                }
-            }
+    const V4<R> pi = P[ii];
+    uint32_t *rowp = S.nl + (size_t)ii * cap;
+    uint4 *row = reinterpret_cast<uint4 *>(rowp);
+    uint32_t b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+    int nf = 0, nb = 0;
+    // entries of the current chunk live in a 4-register shift queue and are
+    // stored as one 16-byte chunk when four have been found
+    auto accept = [&](int j, uint32_t code) {
+        if (code == 0) {
+            b3 = b2; b2 = b1; b1 = b0; b0 = (uint32_t)j;
+            ++nf;
+            if ((nf & 3) == 0 && nf + nb <= cap) row[(nf >> 2) - 1] = make_uint4(b0, b1, b2, b3);
+        } else {
+            if (nf + nb < cap && ((nf + 4) & ~3) + nb < cap) rowp[cap - 1 - nb] = (uint32_t)j | (code << JBITS);
+            ++nb;
         }
-        if (act) {
-            const int need = ((nf + 3) & ~3) + nb;
-            if (need > cap || nb > 0xffff || nf > 0xffff) {
-                C->overflow = 1;
-                S.nl_count[i] = 0;
-            } else {
-                if (nf & 3) {  // sentinel padding of the last chunk
-                    const uint32_t sent = (uint32_t)S.n;
-                    for (int m = nf & 3; m < 4; ++m) { b3 = b2; b2 = b1; b1 = b0; b0 = sent; }
-                    row[nf >> 2] = make_uint4(b0, b1, b2, b3);
+    };
+    for (int dz = N3L ? 0 : -RCH; dz <= RCH; ++dz) {
+        int wz, sz;
+        if (!stencil_cell(cz, dz, nz, S.walls[2], wz, sz)) continue;
+        for (int dy = -RCH; dy <= RCH; ++dy) {
+            // with N3L the half stencil: rows dz > 0, rows (dz = 0, dy > 0),
+            // and in i's own row the cells cx (j > i only) to cx + RCH
+            if (N3L && dz == 0 && dy < 0) continue;
+            const bool own_row = dz == 0 && dy == 0;
+            int wy, sy;
+            if (!stencil_cell(cy, dy, ny, S.walls[1], wy, sy)) continue;
+            int xa = cx - RCH, xb = cx + RCH;
+            if (S.walls[0]) { xa = max(xa, 0); xb = min(xb, nx - 1); }
+            if (N3L && own_row) xa = cx;
+            const int rowc = (wz * ny + wy) * nx;
+            // the run [xa, xb] in unwrapped cell coordinates: the part left of
+            // the box (image -1), inside it (no image), right of it (image +1)
+            for (int sx = -1; sx <= 1; ++sx) {
+                const int a = sx < 0 ? xa : (sx == 0 ? max(xa, 0) : max(xa, nx));
+                const int b = sx < 0 ? min(xb, -1) : (sx == 0 ? min(xb, nx - 1) : xb);
+                if (a > b) continue;
+                int jb = S.cell_start[rowc + a - sx * nx];
+                const int je = S.cell_start[rowc + b - sx * nx + 1];
+                if (N3L && own_row && sx == 0) jb = ii + 1;  // j > i in i's own cell, all j beyond it
+                const uint32_t code = encode_image(sx, sy, sz);
+                // does this run contain i itself without an image?
+                const bool self = !N3L && code == 0 && jb <= ii && ii < je;
+                const R xs = pi.x - (R)sx * S.box[0], ys = pi.y - (R)sy * S.box[1], zs = pi.z - (R)sz * S.box[2];
+                for (int j0 = jb; j0 < je; j0 += 32) {
+                    const int m = min(32, je - j0);
+                    uint32_t mask = 0;
+                    int t = 0;
+                    for (; t + 4 <= m; t += 4) {
+                        const int j = j0 + t;
+                        const V4<R> q0 = ldpos(P, j), q1 = ldpos(P, j + 1), q2 = ldpos(P, j + 2), q3 = ldpos(P, j + 3);
+                        const uint32_t bits = (uint32_t)(r2_of(xs - q0.x, ys - q0.y, zs - q0.z) < S.rlist2) |
+                                              ((uint32_t)(r2_of(xs - q1.x, ys - q1.y, zs - q1.z) < S.rlist2) << 1) |
+                                              ((uint32_t)(r2_of(xs - q2.x, ys - q2.y, zs - q2.z) < S.rlist2) << 2) |
+                                              ((uint32_t)(r2_of(xs - q3.x, ys - q3.y, zs - q3.z) < S.rlist2) << 3);
+                        mask |= bits << t;
+                    }
+                    for (; t < m; ++t) {
+                        const V4<R> q = ldpos(P, j0 + t);
+                        mask |= (uint32_t)(r2_of(xs - q.x, ys - q.y, zs - q.z) < S.rlist2) << t;
+                    }
+                    if (self) {  // drop j == i
+                        const int rel = ii - j0;
+                        if (rel >= 0 && rel < 32) mask &= ~(1u << rel);
+                    }
+                    if (!act) mask = 0;
+                    while (mask) {
+                        const int bit = __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        accept(j0 + bit, code);
+                    }
                 }
-                S.nl_count[i] = nf | (nb << 16);
             }
-            atomicMax(reinterpret_cast<unsigned long long *>(&C->need_cap), (unsigned long long)need);
         }
     }
+    const int need = ((nf + 3) & ~3) + nb;
+    if (act) {
+        if (need > cap || nb > 0xffff || nf > 0xffff) {
+            C->overflow = 1;
+            S.nl_count[i] = 0;
+        } else {
+            if (nf & 3) {  // sentinel padding of the last chunk
+                const uint32_t sent = (uint32_t)S.n;
+                for (int k = nf & 3; k < 4; ++k) { b3 = b2; b2 = b1; b1 = b0; b0 = sent; }
+                row[nf >> 2] = make_uint4(b0, b1, b2, b3);
+            }
+            S.nl_count[i] = nf | (nb << 16);
+        }
+    }
+    block_need_max(C, act ? (unsigned)need : 0u);
 }
 
 // Clusters: each cell's segment is cut into chunks of M consecutive sorted
@@ -408,13 +396,7 @@ __device__ __forceinline__ R box_gap(R loi, R hii, R loj, R hij, int s, R L) {
 // least one particle pair closer than r_list.  With N3L only cj > ci and the
 // cluster itself.
 template <typename R, bool N3L>
-__global__ void k_cp_build(Dev<R> S) {
-    Ctrl *C = S.ctrl;
-    if (!C->rebuild_now) return;
-    const int ci = blockIdx.x * blockDim.x + threadIdx.x;
-    const int ncl = *S.ncl_total;
-    if (ci >= ncl || ci >= S.ncl_cap) return;
-    const V4<R> *P = S.pos[C->pos_par];
+__device__ __forceinline__ int cp_row(const Dev<R> &S, int ci, const V4<R> *P) {
     const V4<R> loi = S.cl_lo[ci], hii = S.cl_hi[ci];
     const int fi = S.cl_first[ci], ni = S.cl_count[ci];
     const int c = S.cl_cell[ci];
@@ -462,9 +444,21 @@ __global__ void k_cp_build(Dev<R> S) {
             }
         }
     }
-    S.cp_count[ci] = cnt < S.cp_cap ? cnt : S.cp_cap;
-    if (cnt > S.cp_cap) C->overflow = 1;
-    atomicMax(reinterpret_cast<unsigned long long *>(&C->need_cap), (unsigned long long)cnt);
+    return cnt;
+}
+template <typename R, bool N3L>
+__global__ void k_cp_build(Dev<R> S) {
+    Ctrl *C = S.ctrl;
+    if (!C->rebuild_now) return;
+    const int ci = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ncl = *S.ncl_total;
+    const bool valid = ci < ncl && ci < S.ncl_cap;
+    const int cnt = valid ? cp_row<R, N3L>(S, ci, S.pos[C->pos_par]) : 0;
+    if (valid) {
+        S.cp_count[ci] = cnt < S.cp_cap ? cnt : S.cp_cap;
+        if (cnt > S.cp_cap) C->overflow = 1;
+    }
+    block_need_max(C, (unsigned)cnt);
 }
 
 __global__ void k_rebuild_finish(Ctrl *C) {
@@ -490,12 +484,17 @@ template <typename R> void launch_scatter(const Dev<R> &S, cudaStream_t st) {
     k_scatter<R><<<div_up(S.n, 256), 256, 0, st>>>(S);
 }
 template <typename R> void launch_sortgather(const Dev<R> &S, cudaStream_t st) {
-    k_sortgather<R><<<div_up((long long)S.ncell * 32, 256), 256, 0, st>>>(S);
+    k_sortgather<R><<<div_up(S.n, 256), 256, 0, st>>>(S);
 }
 template <typename R> void launch_vl_build(const Dev<R> &S, bool n3l, cudaStream_t st) {
     const int blocks = div_up(S.n, VL_BUILD_THREADS);
-    if (n3l) k_vl_build<R, true><<<blocks, VL_BUILD_THREADS, 0, st>>>(S);
-    else k_vl_build<R, false><<<blocks, VL_BUILD_THREADS, 0, st>>>(S);
+    if (S.reach == 1) {
+        if (n3l) k_vl_build<R, true, 1><<<blocks, VL_BUILD_THREADS, 0, st>>>(S);
+        else k_vl_build<R, false, 1><<<blocks, VL_BUILD_THREADS, 0, st>>>(S);
+    } else {
+        if (n3l) k_vl_build<R, true, 2><<<blocks, VL_BUILD_THREADS, 0, st>>>(S);
+        else k_vl_build<R, false, 2><<<blocks, VL_BUILD_THREADS, 0, st>>>(S);
+    }
 }
 template <typename R> void launch_cluster_form(const Dev<R> &S, cudaStream_t st) {
     k_cluster_form<R><<<div_up(S.ncell, 128), 128, 0, st>>>(S);

@@ -303,6 +303,9 @@ template <typename R> void System::fill_dev(Dev<R> &S) const {
         S.box[d] = (R)params.box[d];
         S.box_lo[d] = (R)(params.box[d] - (double)(R)params.box[d]);
         S.boxd[d] = params.box[d];
+        float lf = (float)params.box[d];
+        if ((double)lf > params.box[d]) lf = std::nextafter(lf, 0.0f);
+        S.box_dn[d] = lf;
     }
     S.reach = reach;
     for (int d = 0; d < 3; ++d) S.walls[d] = params.walls[d] ? 1 : 0;

@@ -228,8 +228,8 @@ __device__ bool load_window(const Dev<R> &S, Win<R, G, F> &win, int row, int x0,
         if (G) win.gidx[WIN_CAP] = -1;
         if (F) win.frc[WIN_CAP] = make_pos((R)0, (R)0, (R)0, 0);
     }
-    const bool ok = mbar_wait(&win.mbar, win.phase);
-    __syncthreads();
+    // one verdict for the whole block, so that a timeout ends every thread
+    const bool ok = __syncthreads_and(mbar_wait(&win.mbar, win.phase)) != 0;
     if (threadIdx.x == 0) win.phase ^= 1;
     return ok;
 }
@@ -264,6 +264,7 @@ __global__ void __launch_bounds__(WTHREADS) k_vlw_build(Dev<R> S) {
     const int cap = S.nl_cap, hcap = cap >> 1;
     const int sub = threadIdx.x & 1;
     const unsigned pairmask = 3u << ((threadIdx.x & 31) & ~1);
+    unsigned my_need = 0;  // longest row this thread built
     for (int sidx = blockIdx.x; sidx < nst; sidx += gridDim.x) {
         const int4 st = S.strips[sidx];
         __syncthreads();
@@ -347,9 +348,10 @@ __global__ void __launch_bounds__(WTHREADS) k_vlw_build(Dev<R> S) {
             const int obad = __shfl_xor_sync(pairmask, (int)bad, 1);
             if (sub == 0) S.nl_count[i] = (bad || obad) ? 0 : (int)(mine | (other << 16));
             if (bad) C->overflow = 1;
-            atomicMax(reinterpret_cast<unsigned long long *>(&C->need_cap), (unsigned long long)(2 * need));
+            my_need = max(my_need, (unsigned)(2 * need));
         }
     }
+    warp_need_max(C, my_need);
 }
 
 template <typename R> struct WTab {

@@ -46,6 +46,9 @@ CONFIGS = [
     dict(method="VL", newton3=False, threads_per_unit=4),
     dict(method="VL", newton3=True, threads_per_unit=1),
     dict(method="VL", newton3=True, threads_per_unit=4),
+    dict(method="VL", newton3=False, threads_per_unit=1, csf=0.5),
+    dict(method="VL", newton3=False, threads_per_unit=2, csf=0.5),
+    dict(method="VL", newton3=True, threads_per_unit=1, csf=0.5),
     dict(method="VLW", newton3=False),
     dict(method="VLW", newton3=True),
     dict(method="CL", cluster_size=4, newton3=False, threads_per_unit=4),
@@ -209,12 +212,14 @@ def test_graph_equals_eager(lj):
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
 
 
-def test_displacement_forces_early_rebuild(lj):
+@pytest.mark.parametrize("cfg", [dict(method="VL"), dict(method="VL", csf=0.5), dict(method="VL", newton3=True, csf=0.5)],
+                         ids=["csf1", "csf0.5", "n3-csf0.5"])
+def test_displacement_forces_early_rebuild(lj, cfg):
     # hot gas: particles cross skin/2 long before R = 200 steps; the FP64 run
     # stays on the oracle's trajectory, so no pair was missed
     sc = scenarios.random_gas(800, 14.0, seed=41, min_dist=0.9, temperature=6.0)
     s = lj.System(sc, skin=0.2, precision=1)
-    s.set_config(method="VL", rebuild_interval=200)
+    s.set_config(rebuild_interval=200, **cfg)
     s.step(120)
     c = s.counters()
     assert c["early_rebuilds"] >= 2, c
@@ -341,7 +346,8 @@ def test_liquid_1m_full_size(lj):
     configuration: whole pair set and all forces against the oracle."""
     sc = scenarios.liquid_1m()
     x1 = drift(sc["x"], sc["box"], 81, 0.9 * 0.5 * sc["skin"])
-    for cfg in (dict(method="VL"), dict(method="VLW"), dict(method="VLW", newton3=True)):
+    for cfg in (dict(method="VL"), dict(method="VL", csf=0.5), dict(method="VL", newton3=True, csf=0.5),
+                dict(method="VLW"), dict(method="VLW", newton3=True)):
         s = lj.System(sc)
         s.set_config(rebuild_interval=10, **cfg)
         check_against_oracle(s, sc, sc["x"], forces=False)  # perfect fcc lattice: all forces vanish
@@ -350,15 +356,19 @@ def test_liquid_1m_full_size(lj):
         s.close()
 
 
-@pytest.mark.parametrize("method", ["VL", "LC", "CL", "VLW"])
-def test_smallest_boxes_twenty_seeds(lj, method):
+SMALL_BOX_CFGS = [dict(method="VL"), dict(method="VL", newton3=True), dict(method="VL", csf=0.5),
+                  dict(method="VL", newton3=True, csf=0.5), dict(method="LC"), dict(method="LC", csf=0.5),
+                  dict(method="CL", cluster_size=4, threads_per_unit=4), dict(method="VLW")]
+
+
+@pytest.mark.parametrize("cfg", SMALL_BOX_CFGS, ids=lambda c: "-".join("%s%s" % kv for kv in c.items()))
+def test_smallest_boxes_twenty_seeds(lj, cfg):
     """The smallest box the library accepts (L = 2 (r_c + skin)(1 + 2^-10),
-    plus 0.01): two cells per side, every stencil wraps onto the same cells
-    with two images; 20 seeded random gases, pair sets and forces exact."""
+    plus 0.01): two cells per side (four at CSF 0.5), every stencil wraps
+    onto the same cells with two images; 20 seeded random gases, pair sets
+    and forces exact."""
     L = 2 * 2.8 * (1 + 1.0 / 1024) + 0.01
-    kw = dict(method=method, rebuild_interval=10)
-    if method == "CL":
-        kw.update(cluster_size=4, threads_per_unit=4)
+    kw = dict(cfg, rebuild_interval=10)
     for seed in range(20):
         sc = scenarios.random_gas(120, L, seed=100 + seed, min_dist=0.8)
         s = lj.System(sc)

@@ -15,7 +15,8 @@ from paper_2505_03438_gb300 import scenarios
 pytestmark = pytest.mark.gpu
 
 CONFIGS = [dict(method="LC"), dict(method="LC", newton3=True), dict(method="LC", csf=0.5),
-           dict(method="VL"), dict(method="VL", threads_per_unit=4), dict(method="VL", newton3=True)]
+           dict(method="VL"), dict(method="VL", threads_per_unit=4), dict(method="VL", newton3=True),
+           dict(method="VL", csf=0.5), dict(method="VL", newton3=True, csf=0.5)]
 
 
 def _gas(seed, L=11.0, n=500):
