@@ -235,8 +235,10 @@ def inhomogeneous_leg(steps=20000, every=1000, strategy="predictive", fixed_step
     0.01, T 1.2), periodic box 200, about 292k particles: `steps` steps with
     a tuning phase every `every` steps (trial steps count as steps; a phase
     whose live statistics moved less than skip_within since the last phase
-    with trials is skipped), against every fixed configuration run over the
-    same steps from the same state."""
+    with trials is skipped), once with `strategy` and once with the Random
+    Forest strategy (the shipped forest, one configuration trialled a phase),
+    against every fixed configuration run over the same steps from the same
+    state."""
     import torch
 
     import paper_2505_03438_gb300 as lj
@@ -255,20 +257,28 @@ def inhomogeneous_leg(steps=20000, every=1000, strategy="predictive", fixed_step
         torch.cuda.synchronize()
         return a.elapsed_time(b)
 
-    s = lj.System(sc, stream=stream.cuda_stream)
-    s.step(3)
-    phases = []
+    def tuned_run(strat, phases):
+        s = lj.System(sc, stream=stream.cuda_stream)
+        s.step(3)
+        if strat == "forest":
+            s.set_forest()
 
-    def tuned_run():
-        for k in range(steps // every):
-            c, rep = s.autotune(strategy=strategy, trial_steps=5, probe_steps=2, probe_factor=2.0,
-                                skip_within=skip_within)
-            s.step(every - rep["trial_steps_total"])
-            phases.append({"step": k * every, "chosen": c.name(), "ntrialled": rep["ntrialled"],
-                           "skipped": rep["skipped"], "phase_ms": rep["phase_ms"], "overhead_ms": rep["overhead_ms"]})
+        def run():
+            for k in range(steps // every):
+                c, rep = s.autotune(strategy=strat, trial_steps=5, probe_steps=2, probe_factor=2.0,
+                                    skip_within=skip_within)
+                s.step(every - rep["trial_steps_total"])
+                phases.append({"step": k * every, "chosen": c.name(), "ntrialled": rep["ntrialled"],
+                               "skipped": rep["skipped"], "phase_ms": rep["phase_ms"],
+                               "overhead_ms": rep["overhead_ms"]})
 
-    ms = timed(tuned_run)
-    s.close()
+        ms = timed(run)
+        s.close()
+        return ms
+
+    phases, phases_rf = [], []
+    ms = tuned_run(strategy, phases)
+    ms_rf = tuned_run("forest", phases_rf)
     # fixed configurations: every candidate screened over the first
     # `screen` steps, the best five run over all `steps` from the same state
     probe = lj.System(sc)
@@ -300,6 +310,10 @@ def inhomogeneous_leg(steps=20000, every=1000, strategy="predictive", fixed_step
             "phases_skipped": sum(p["skipped"] for p in phases),
             "tuning_overhead_ms": sum(p["overhead_ms"] for p in phases),
             "tuning_phase_ms": sum(p["phase_ms"] for p in phases), "phases": phases,
+            "forest": {"value": n * steps / (ms_rf * 1e-3), "strategy": "forest", "forest_top": 1,
+                       "phases_skipped": sum(p["skipped"] for p in phases_rf),
+                       "tuning_overhead_ms": sum(p["overhead_ms"] for p in phases_rf),
+                       "tuning_phase_ms": sum(p["phase_ms"] for p in phases_rf), "phases": phases_rf},
             "fixed_screen_steps": screen, "fixed_screened": {k: v[1] for k, v in screened.items()},
             "fixed": fixed, "best_fixed": best}
 
@@ -326,6 +340,7 @@ def run_ours(args):
     import torch
 
     import paper_2505_03438_gb300 as lj
+    from paper_2505_03438_gb300 import forest as lj_forest
     from paper_2505_03438_gb300 import scenarios
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -363,7 +378,10 @@ def run_ours(args):
 
     def timed(hh, strategy):
         """Timed region: one tuning phase (its trial steps count) + the rest of
-        the K steps, bracketed by a barrier and device synchronisation."""
+        the K steps, bracketed by a barrier and device synchronisation.  The
+        Random Forest strategy's forest is installed before it."""
+        if strategy == "forest":
+            lj.ljsel_set_forest(hh, lj_forest.load())
         c0 = lj.ljsel_get_counters(hh)
         barrier()
         torch.cuda.synchronize()
@@ -388,7 +406,7 @@ def run_ours(args):
                 "rebuilds": c1["rebuilds"] - c0["rebuilds"], "early": c1["early_rebuilds"] - c0["early_rebuilds"]}
 
     headline = args.strategy if args.tune else None
-    other = [st for st in ("expert", "full") if args.tune and args.other and st != headline]
+    other = [st for st in ("expert", "full", "forest") if args.tune and args.other and st != headline]
     # the other strategy first, so the headline run is the last before profiling
     extra_runs = {}
     for st in other:
@@ -542,8 +560,8 @@ def main():
     ap.add_argument("--csf", type=float, default=1.0, help="with --method: cell size factor (1.0 or 0.5)")
     ap.add_argument("--trial-steps", type=int, default=5)
     ap.add_argument("--probe-steps", type=int, default=2)
-    ap.add_argument("--strategy", default="expert", choices=["full", "predictive", "expert"],
-                    help="tuning strategy of the headline run (the other of expert/full is reported beside it)")
+    ap.add_argument("--strategy", default="expert", choices=["full", "predictive", "expert", "forest"],
+                    help="tuning strategy of the headline run (the others of expert/full/forest are reported beside it)")
     ap.add_argument("--fixed-steps", type=int, default=-1, help="steps per fixed configuration (-1: same as --steps)")
     ap.add_argument("--profile-steps", type=int, default=60)
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")

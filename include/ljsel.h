@@ -139,11 +139,15 @@ typedef struct ljsel_counters {
 } ljsel_counters;
 
 /* Autotuner options (Sec. 2.2.5 Full Search, Sec. 5.1 Predictive, Sec. 5.2
- * Expert).                                                                */
+ * Expert, Sec. 5.3 Random Forest).                                        */
 typedef struct ljsel_tuner_opts {
     int32_t strategy;          /* 0: full search; 1: predictive; 2: expert
                                   (fuzzy rules on the mean particles per
-                                  CSF-1 bin, Sec. 4 statistics)               */
+                                  CSF-1 bin, Sec. 4 statistics); 3: random
+                                  forest (the forest installed with
+                                  ljsel_set_forest ranks its configurations
+                                  from the Sec. 4 statistics; the forest_top
+                                  most probable are trialled)                 */
     int32_t trial_steps;       /* steps per trial (>= 1); a trial first
                                   rebuilds, then advances trial_steps steps   */
     double predict_factor;     /* predictive: trial configs predicted within
@@ -158,7 +162,9 @@ typedef struct ljsel_tuner_opts {
                                   cost is above probe_factor x the best cost
                                   of the phase so far, the trial stops there
                                   (0: always run trial_steps)                 */
-    int32_t reserved;
+    int32_t forest_top;        /* random forest: configurations trialled per
+                                  phase, most probable first (>= 1; 0 counts
+                                  as 1)                                       */
     double probe_factor;       /* e.g. 2.0                                     */
     double skip_within;        /* > 0: when the live statistics (mean,
                                   relative std and max particles per CSF-1
@@ -180,7 +186,8 @@ typedef struct ljsel_tuner_report {
     int64_t trial_steps_total; /* steps advanced by trials in the last phase  */
     int32_t nprobed_out;       /* trials stopped after their probe            */
     int32_t skipped;           /* 1: the phase was skipped (skip_within)      */
-    double expert_input;       /* expert: mean particles per CSF-1 bin        */
+    double expert_input;       /* expert: mean particles per CSF-1 bin; random
+                                  forest: probability of its first choice     */
 } ljsel_tuner_report;
 
 /* GPU time per kernel class, measured with CUDA events around each launch
@@ -288,6 +295,47 @@ ljsel_status ljsel_get_counters(ljsel_system s, ljsel_counters *c);
  * strategy) persists across phases of the same handle.                    */
 ljsel_status ljsel_autotune(ljsel_system s, const ljsel_tuner_opts *opts,
                             ljsel_config *chosen, ljsel_tuner_report *report);
+
+/* A random-forest classifier (Sec. 5.3) over the live statistics: the
+ * feature vector is the fields of ljsel_stats in order (mean, rel_std,
+ * median, max, nbins, nempty, skin, threads; the first nfeatures of them).
+ * Node k of the flattened trees either splits (feature[k] in 0..nfeatures-1:
+ * go to left[k] when x[feature[k]] <= threshold[k], else to right[k]) or is
+ * a leaf (feature[k] = -1) holding class probabilities value[k * nclasses +
+ * c].  Class c names the configuration classes[c].  All arrays are host
+ * memory owned by the caller.                                             */
+typedef struct ljsel_forest {
+    int32_t ntrees;
+    int32_t nclasses;
+    int32_t nfeatures;         /* 1..8                                         */
+    int32_t nnodes;            /* nodes over all trees                         */
+    const int32_t *root;       /* [ntrees] root node of each tree              */
+    const int32_t *feature;    /* [nnodes] split feature, -1 at a leaf         */
+    const double *threshold;   /* [nnodes]                                     */
+    const int32_t *left;       /* [nnodes] (leaves: ignored)                   */
+    const int32_t *right;      /* [nnodes] (leaves: ignored)                   */
+    const double *value;       /* [nnodes * nclasses] leaf class probabilities */
+    const ljsel_config *classes; /* [nclasses]                                 */
+} ljsel_forest;
+
+/* Class probabilities of the forest for one feature vector x[nfeatures]:
+ * the mean over the trees of the leaf each tree reaches.  Host only (no
+ * GPU).  proba: host, nclasses doubles.  LJSEL_ERR_ARG for a NULL pointer
+ * or a malformed forest (a root, child or feature out of range, a negative
+ * or non-finite leaf value, a path longer than nnodes).                   */
+ljsel_status ljsel_forest_predict(const ljsel_forest *f, const double *x, double *proba);
+
+/* Install (copy) a forest in the system for the Random Forest strategy;
+ * the same checks as ljsel_forest_predict, and every class must be a valid
+ * configuration for this system (LJSEL_ERR_UNSUPPORTED otherwise).        */
+ljsel_status ljsel_set_forest(ljsel_system s, const ljsel_forest *f);
+
+/* Cost per step (ms) measured for each configuration in its most recent
+ * trial (the cost the tuner compares), for the configurations trialled so
+ * far: writes up to cap configurations and costs, *count = their number.
+ * Host only; the phase of the last trial goes to phase[k] (may be NULL).  */
+ljsel_status ljsel_tuner_costs(ljsel_system s, int32_t cap, ljsel_config *cfgs, double *cost, int32_t *phase,
+                               int32_t *count);
 
 /* The trial set of one Predictive tuning phase (Sec. 5.1), host only (no
  * GPU, no handle); ljsel_autotune applies the same rule.  Before phase 2

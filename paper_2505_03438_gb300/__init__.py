@@ -73,6 +73,18 @@ class ljsel_config(ctypes.Structure):
                                          self.rebuild_interval, self.csf)
 
 
+def config_from_name(name):
+    """The configuration a name of ljsel_config.name() denotes, e.g.
+    'VL-noN3L-t2-R10-csf1' or 'CL8-N3L-t8-R10-csf1'."""
+    import re
+    m = re.match(r"^(LC|VLW|VL|CL)(\d+)?-(N3L|noN3L)-t(\d+)-R(\d+)-csf([0-9.]+)$", name)
+    if not m:
+        raise ValueError("not a configuration name: %r" % name)
+    meth, M, n3, t, R, csf = m.groups()
+    return make_config(meth, cluster_size=int(M) if M else 1, newton3=(n3 == "N3L"), threads_per_unit=int(t),
+                       rebuild_interval=int(R), csf=float(csf))
+
+
 class ljsel_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in ("mean", "rel_std", "median", "max", "nbins", "nempty", "skin",
                                                 "threads")]
@@ -94,9 +106,25 @@ class ljsel_tuner_opts(ctypes.Structure):
         ("ncandidates", ctypes.c_int32),
         ("candidates", ctypes.POINTER(ljsel_config)),
         ("probe_steps", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("forest_top", ctypes.c_int32),
         ("probe_factor", ctypes.c_double),
         ("skip_within", ctypes.c_double),
+    ]
+
+
+class ljsel_forest(ctypes.Structure):
+    _fields_ = [
+        ("ntrees", ctypes.c_int32),
+        ("nclasses", ctypes.c_int32),
+        ("nfeatures", ctypes.c_int32),
+        ("nnodes", ctypes.c_int32),
+        ("root", ctypes.c_void_p),
+        ("feature", ctypes.c_void_p),
+        ("threshold", ctypes.c_void_p),
+        ("left", ctypes.c_void_p),
+        ("right", ctypes.c_void_p),
+        ("value", ctypes.c_void_p),
+        ("classes", ctypes.POINTER(ljsel_config)),
     ]
 
 
@@ -183,6 +211,10 @@ _SIGS = {
                              ctypes.c_int),
     "ljsel_predictive_trials": ([ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.c_int32, ctypes.c_double,
                                  ctypes.c_int32, _P], ctypes.c_int),
+    "ljsel_forest_predict": ([ctypes.POINTER(ljsel_forest), _P, _P], ctypes.c_int),
+    "ljsel_set_forest": ([_P, ctypes.POINTER(ljsel_forest)], ctypes.c_int),
+    "ljsel_tuner_costs": ([_P, ctypes.c_int32, ctypes.POINTER(ljsel_config), _P, _P, ctypes.POINTER(ctypes.c_int32)],
+                          ctypes.c_int),
 }
 EXPORTED = tuple(_SIGS)
 _lib = None
@@ -408,10 +440,11 @@ def ljsel_default_candidates(h):
 
 
 def ljsel_autotune(h, strategy=0, trial_steps=10, predict_factor=2.0, blacklist_factor=10.0, retrial_phases=4,
-                   candidates=None, probe_steps=0, probe_factor=2.0, skip_within=0.0):
+                   candidates=None, probe_steps=0, probe_factor=2.0, skip_within=0.0, forest_top=1):
     o = ljsel_tuner_opts()
     o.skip_within = float(skip_within)
-    o.strategy = {"full": 0, "predictive": 1, "expert": 2}.get(strategy, strategy)
+    o.forest_top = int(forest_top)
+    o.strategy = {"full": 0, "predictive": 1, "expert": 2, "forest": 3}.get(strategy, strategy)
     o.probe_steps = int(probe_steps)
     o.probe_factor = float(probe_factor)
     o.trial_steps = int(trial_steps)
@@ -451,6 +484,59 @@ def ljsel_predictive_trials(phase, history, last_trial_phase, blacklisted, incum
                                          bl.ctypes.data, int(incumbent), float(predict_factor), int(retrial_phases),
                                          out.ctypes.data))
     return out[:n].tolist()
+
+
+def _forest_struct(model):
+    """ljsel_forest over the arrays of a forest model (dict of numpy arrays,
+    see paper_2505_03438_gb300.forest); the arrays are kept alive on the
+    returned struct."""
+    keep = {
+        "root": np.ascontiguousarray(model["root"], np.int32),
+        "feature": np.ascontiguousarray(model["feature"], np.int32),
+        "threshold": np.ascontiguousarray(model["threshold"], np.float64),
+        "left": np.ascontiguousarray(model["left"], np.int32),
+        "right": np.ascontiguousarray(model["right"], np.int32),
+        "value": np.ascontiguousarray(model["value"], np.float64),
+    }
+    names = list(model["classes"])
+    cls = (ljsel_config * max(len(names), 1))(*[config_from_name(c) for c in names])
+    f = ljsel_forest()
+    f.ntrees = len(keep["root"])
+    f.nclasses = len(names)
+    f.nfeatures = int(model["nfeatures"])
+    f.nnodes = len(keep["feature"])
+    for k, a in keep.items():
+        setattr(f, k, a.ctypes.data)
+    f.classes = cls
+    f._keep = (keep, cls)
+    return f
+
+
+def ljsel_forest_predict(model, x):
+    """Class probabilities of a forest model for one feature vector (host)."""
+    f = _forest_struct(model)
+    xv = np.ascontiguousarray(x, np.float64)
+    out = np.zeros(max(f.nclasses, 1))
+    _check(lib().ljsel_forest_predict(ctypes.byref(f), xv.ctypes.data, out.ctypes.data))
+    return out[:f.nclasses]
+
+
+def ljsel_set_forest(h, model):
+    f = _forest_struct(model)
+    _check(lib().ljsel_set_forest(h, ctypes.byref(f)))
+
+
+def ljsel_tuner_costs(h):
+    """{configuration name: (cost ms per step, phase)} of every configuration
+    trialled so far, from its most recent trial."""
+    cnt = ctypes.c_int32()
+    _check(lib().ljsel_tuner_costs(h, 0, None, None, None, ctypes.byref(cnt)))
+    n = cnt.value
+    cfgs = (ljsel_config * max(n, 1))()
+    cost = np.zeros(max(n, 1))
+    ph = np.zeros(max(n, 1), np.int32)
+    _check(lib().ljsel_tuner_costs(h, n, cfgs, cost.ctypes.data, ph.ctypes.data, ctypes.byref(cnt)))
+    return {cfgs[k].name(): (float(cost[k]), int(ph[k])) for k in range(n)}
 
 
 def _table(a, nt):
@@ -575,6 +661,14 @@ class System:
 
     def stats(self):
         return ljsel_get_stats(self.h)
+
+    def set_forest(self, model=None):
+        """Install a random-forest model (a dict of paper_2505_03438_gb300.forest;
+        None: the model shipped with the package) for autotune(strategy="forest")."""
+        if model is None:
+            from . import forest
+            model = forest.load()
+        ljsel_set_forest(self.h, model)
 
     def counters(self):
         return ljsel_get_counters(self.h)

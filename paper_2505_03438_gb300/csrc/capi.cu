@@ -114,6 +114,48 @@ std::vector<ljsel_config> default_candidates(const System &s) {
     return v;
 }
 
+// Random forest (Sec. 5.3): structural checks, then the mean over the trees
+// of the class probabilities at the leaf each tree reaches.
+ljsel_status forest_check(const ljsel_forest *f) {
+    if (!f || f->ntrees < 1 || f->nclasses < 1 || f->nfeatures < 1 || f->nfeatures > 8 || f->nnodes < 1 || !f->root ||
+        !f->feature || !f->threshold || !f->left || !f->right || !f->value || !f->classes) {
+        set_error("malformed forest: counts or NULL arrays");
+        return LJSEL_ERR_ARG;
+    }
+    for (int t = 0; t < f->ntrees; ++t)
+        if (f->root[t] < 0 || f->root[t] >= f->nnodes) { set_error("forest root out of range"); return LJSEL_ERR_ARG; }
+    for (int k = 0; k < f->nnodes; ++k) {
+        const int ft = f->feature[k];
+        if (ft == -1) {
+            for (int c = 0; c < f->nclasses; ++c) {
+                const double v = f->value[(size_t)k * f->nclasses + c];
+                if (!(v >= 0.0) || !std::isfinite(v)) { set_error("forest leaf value negative or not finite"); return LJSEL_ERR_ARG; }
+            }
+        } else if (ft < 0 || ft >= f->nfeatures || f->left[k] < 0 || f->left[k] >= f->nnodes || f->right[k] < 0 ||
+                   f->right[k] >= f->nnodes || !std::isfinite(f->threshold[k])) {
+            set_error("forest split node out of range");
+            return LJSEL_ERR_ARG;
+        }
+    }
+    return LJSEL_OK;
+}
+ljsel_status forest_predict(int ntrees, int ncls, int nnodes, const int32_t *root, const int32_t *feature,
+                            const double *threshold, const int32_t *left, const int32_t *right, const double *value,
+                            const double *x, double *proba) {
+    for (int c = 0; c < ncls; ++c) proba[c] = 0.0;
+    for (int t = 0; t < ntrees; ++t) {
+        int k = root[t];
+        int steps = 0;
+        while (feature[k] >= 0) {
+            k = x[feature[k]] <= threshold[k] ? left[k] : right[k];
+            if (++steps > nnodes) { set_error("forest path longer than its nodes (a cycle)"); return LJSEL_ERR_ARG; }
+        }
+        for (int c = 0; c < ncls; ++c) proba[c] += value[(size_t)k * ncls + c];
+    }
+    for (int c = 0; c < ncls; ++c) proba[c] /= ntrees;
+    return LJSEL_OK;
+}
+
 // Trial set of one Predictive phase (Sec. 5.1); see ljsel_predictive_trials.
 ljsel_status predictive_trials(int32_t ncand, int32_t phase, const int32_t *hist_n, const int32_t *hist_phase,
                                const double *hist_cost, const int32_t *last_trial_phase, const int32_t *blacklisted,
@@ -161,6 +203,56 @@ ljsel_status predictive_trials(int32_t ncand, int32_t phase, const int32_t *hist
 extern "C" {
 
 const char *ljsel_last_error(void) { return last_error(); }
+
+ljsel_status ljsel_forest_predict(const ljsel_forest *f, const double *x, double *proba) {
+    set_error("");
+    if (!x || !proba) { set_error("NULL argument"); return LJSEL_ERR_ARG; }
+    TRY(forest_check(f));
+    return forest_predict(f->ntrees, f->nclasses, f->nnodes, f->root, f->feature, f->threshold, f->left, f->right,
+                          f->value, x, proba);
+}
+
+ljsel_status ljsel_set_forest(ljsel_system h, const ljsel_forest *f) {
+    System *s = (System *)h;
+    if (!s) { set_error("NULL handle"); return LJSEL_ERR_ARG; }
+    set_error("");
+    TRY(forest_check(f));
+    for (int c = 0; c < f->nclasses; ++c) {
+        const ljsel_status st = validate_config(*s, &f->classes[c]);
+        if (st != LJSEL_OK) return st;
+    }
+    Forest &F = s->forest;
+    F.ntrees = f->ntrees;
+    F.ncls = f->nclasses;
+    F.nfeat = f->nfeatures;
+    F.nnodes = f->nnodes;
+    F.root.assign(f->root, f->root + f->ntrees);
+    F.feature.assign(f->feature, f->feature + f->nnodes);
+    F.left.assign(f->left, f->left + f->nnodes);
+    F.right.assign(f->right, f->right + f->nnodes);
+    F.threshold.assign(f->threshold, f->threshold + f->nnodes);
+    F.value.assign(f->value, f->value + (size_t)f->nnodes * f->nclasses);
+    F.classes.assign(f->classes, f->classes + f->nclasses);
+    return LJSEL_OK;
+}
+
+ljsel_status ljsel_tuner_costs(ljsel_system h, int32_t cap, ljsel_config *cfgs, double *cost, int32_t *phase,
+                               int32_t *count) {
+    System *s = (System *)h;
+    if (!s || !count || (cap > 0 && (!cfgs || !cost))) { set_error("invalid argument"); return LJSEL_ERR_ARG; }
+    int k = 0;
+    for (const TunerEntry &e : s->tuner) {
+        if (e.history.empty()) continue;
+        if (k < cap) {
+            cfgs[k] = e.cfg;
+            cost[k] = e.history.back().second;
+            if (phase) phase[k] = e.history.back().first;
+        }
+        ++k;
+    }
+    *count = k;
+    return LJSEL_OK;
+}
 
 ljsel_status ljsel_predictive_trials(int32_t ncand, int32_t phase, const int32_t *hist_n, const int32_t *hist_phase,
                                      const double *hist_cost, const int32_t *last_trial_phase,
@@ -680,15 +772,20 @@ ljsel_status ljsel_autotune(ljsel_system h, const ljsel_tuner_opts *opts, ljsel_
                             ljsel_tuner_report *report) {
     System *s = (System *)h;
     if (!s || !opts) { set_error("NULL argument"); return LJSEL_ERR_ARG; }
-    if (opts->trial_steps < 1 || opts->strategy < 0 || opts->strategy > 2 || opts->probe_steps < 0) {
+    if (opts->trial_steps < 1 || opts->strategy < 0 || opts->strategy > 3 || opts->probe_steps < 0 ||
+        opts->forest_top < 0) {
         set_error("invalid tuner options");
         return LJSEL_ERR_ARG;
+    }
+    if (opts->strategy == 3 && s->forest.ntrees == 0) {
+        set_error("the random forest strategy needs a forest (ljsel_set_forest)");
+        return LJSEL_ERR_STATE;
     }
     auto t0 = std::chrono::steady_clock::now();
     if (!(opts->skip_within >= 0)) { set_error("skip_within must be >= 0"); return LJSEL_ERR_ARG; }
     // live statistics: the expert input, and the test for skipping a phase
     ljsel_stats st_now{};
-    const bool need_stats = opts->strategy == 2 || opts->skip_within > 0;
+    const bool need_stats = opts->strategy == 2 || opts->strategy == 3 || opts->skip_within > 0;
     if (need_stats) TRY(ljsel_get_stats(h, &st_now));
     if (opts->skip_within > 0 && s->have_tuned_stats) {
         auto close = [&](double a, double b) { return std::fabs(a - b) <= opts->skip_within * std::max(std::fabs(b), 1e-12); };
@@ -709,7 +806,9 @@ ljsel_status ljsel_autotune(ljsel_system h, const ljsel_tuner_opts *opts, ljsel_
         }
     }
     std::vector<ljsel_config> cands;
-    if (opts->ncandidates > 0) {
+    if (opts->strategy == 3) {
+        cands = s->forest.classes;  // the forest ranks its own classes
+    } else if (opts->ncandidates > 0) {
         if (!opts->candidates) { set_error("candidates is NULL"); return LJSEL_ERR_ARG; }
         for (int k = 0; k < opts->ncandidates; ++k) {
             TRY(validate_config(*s, &opts->candidates[k]));
@@ -741,6 +840,28 @@ ljsel_status ljsel_autotune(ljsel_system h, const ljsel_tuner_opts *opts, ljsel_
         }
         if (!any)
             for (size_t k = 0; k < cands.size(); ++k) trial[k] = !ent[k]->blacklisted;
+    } else if (opts->strategy == 3) {
+        // Random Forest (Sec. 5.3): class probabilities from the Sec. 4
+        // statistics; the forest_top most probable classes are trialled
+        const Forest &F = s->forest;
+        const double x[8] = {st_now.mean, st_now.rel_std, st_now.median, st_now.max,
+                             st_now.nbins, st_now.nempty, st_now.skin, st_now.threads};
+        std::vector<double> proba(F.ncls, 0.0);
+        TRY(forest_predict(F.ntrees, F.ncls, F.nnodes, F.root.data(), F.feature.data(), F.threshold.data(),
+                           F.left.data(), F.right.data(), F.value.data(), x, proba.data()));
+        std::vector<int> rank(F.ncls);
+        for (int c = 0; c < F.ncls; ++c) rank[c] = c;
+        std::stable_sort(rank.begin(), rank.end(), [&](int a, int b) { return proba[a] > proba[b]; });
+        const int top = std::max(1, opts->forest_top);
+        for (size_t k = 0; k < cands.size(); ++k) trial[k] = 0;
+        int taken = 0;
+        for (int r = 0; r < F.ncls && taken < top; ++r) {
+            if (ent[rank[r]]->blacklisted) continue;
+            trial[rank[r]] = 1;
+            ++taken;
+        }
+        if (!taken) trial[rank[0]] = 1;  // everything blacklisted: keep the forest's first choice
+        expert_x = proba[rank[0]];
     } else if (opts->strategy == 1) {
         const int nc = (int)cands.size();
         std::vector<int32_t> hn(nc), hp(2 * nc, 0), lt(nc), bl(nc), tr(nc);

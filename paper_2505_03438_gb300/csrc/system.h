@@ -28,6 +28,15 @@ struct TunerEntry {
     bool blacklisted = false;
 };
 
+// A random-forest classifier installed for the Random Forest strategy
+// (Sec. 5.3), copied from a caller's ljsel_forest.
+struct Forest {
+    int ntrees = 0, ncls = 0, nfeat = 0, nnodes = 0;
+    std::vector<int32_t> root, feature, left, right;
+    std::vector<double> threshold, value;
+    std::vector<ljsel_config> classes;
+};
+
 // One instantiated step graph, valid for exactly the configuration and
 // device layout (the bytes of the kernel-parameter block) it was built for.
 struct GraphEntry {
@@ -84,6 +93,7 @@ struct System {
     // tuner state
     std::vector<TunerEntry> tuner;
     int tuner_phase = 0;
+    Forest forest;  // Random Forest strategy (empty until ljsel_set_forest)
     ljsel_tuner_report last_report{};
     bool have_tuned_stats = false;
     ljsel_stats tuned_stats{};  // live statistics at the last phase that ran trials

@@ -187,12 +187,12 @@ def jittered_mixture(nside=7, seed=5, jitter=0.1):
     return sc
 
 
-def _rsa(center, radius, box_len, target, dmin, rng, existing=None, inside=True):
+def _rsa(center, radius, box_len, target, dmin, rng, existing=None, inside=True, min_batch=40000):
     """Random sequential addition in batches: uniform candidates, accepted
     when no accepted point lies closer than dmin (minimum image); of two
     candidates of one batch closer than dmin the later one is dropped.
     inside=True draws in the ball (center, radius); inside=False draws in the
-    periodic box outside it."""
+    periodic box outside it.  Batches hold at least min_batch candidates."""
     from scipy.spatial import cKDTree
     acc = np.zeros((0, 3)) if existing is None else np.asarray(existing, np.float64)
     n0 = len(acc)
@@ -207,7 +207,7 @@ def _rsa(center, radius, box_len, target, dmin, rng, existing=None, inside=True)
         if tries > 100000:
             raise RuntimeError("RSA placement stalled")
         left = target - (len(acc) - n0)
-        batch = int(min(max(40000, 1.5 * left / max(rate, 1e-3)), 400000))
+        batch = int(min(max(min_batch, 1.5 * left / max(rate, 1e-3)), 400000))
         if inside:
             u = rng.normal(size=(batch, 3))
             u /= np.linalg.norm(u, axis=1, keepdims=True)
@@ -274,3 +274,75 @@ def _heated_sphere_draw(seed, box_len, radius, rho_liquid, t_liquid, rho_vapour,
     vl = maxwell_boltzmann(n_l, t_liquid, 1.0, rng)
     vv = maxwell_boltzmann(n_v, t_vapour, 1.0, rng)
     return xa, np.concatenate([vl, vv]), n_l
+
+
+def _with_vapour(xd, box_len, rho_vapour, dmin, rng):
+    """Dense points xd plus a vapour of the given density placed around them
+    by random sequential addition (no vapour point closer than dmin to any)."""
+    n_v = int(round(rho_vapour * box_len ** 3))
+    if n_v == 0:
+        return np.asarray(xd, np.float64)
+    return _rsa(np.full(3, 0.5 * box_len), 0.0, box_len, n_v, dmin, rng, existing=xd, inside=False)
+
+
+def training_scenarios(seed=7, dmin=0.9, rc=2.5, dt=0.005, rebuild=10):
+    """Synthetic scenarios for the data behind the Random Forest strategy, of
+    the paper's kinds (Sec. 5.3: uniform gases, clustered particles, a dense
+    cuboid in a gas, spheres in a large box, an almost empty box), scaled to
+    r_c = 2.5 and to sizes of 10^3 to 4.4 x 10^5 particles.  Placement keeps
+    a minimum spacing dmin so that trial steps stay physical; skins cycle
+    through 0.1 ... 0.5 as in the paper's data.  Yields scenario dicts."""
+    rng = np.random.default_rng(seed)
+    skins = [0.1, 0.2, 0.3, 0.4, 0.5]
+    k = [0]
+
+    def make(name, x, box_len, temperature):
+        x = np.mod(np.asarray(x, np.float64), box_len)
+        n = len(x)
+        v = maxwell_boltzmann(n, temperature, 1.0, rng)
+        skin = skins[k[0] % len(skins)]
+        k[0] += 1
+        sc = dict(name=name, x=x, v=v, types=np.zeros(n, np.int32), dt=dt, skin=skin, rebuild=rebuild,
+                  temperature=temperature)
+        sc.update(_single_type(np.full(3, box_len), rc))
+        return sc
+
+    # uniform gases (random sequential addition)
+    for box_len in (30.0, 60.0):
+        for rho in (0.005, 0.02, 0.05, 0.1, 0.2, 0.35):
+            n = int(round(rho * box_len ** 3))
+            x = _rsa(np.full(3, 0.5 * box_len), 0.0, box_len, n, dmin, rng, inside=False)
+            yield make("gas_L%g_rho%g" % (box_len, rho), x, box_len, 1.2)
+    # liquids and dense solids (jittered fcc)
+    for nside in (10, 20, 32, 48):
+        for rho in (0.6, 0.75, 0.9, 1.0):
+            x, box = fcc_lattice(nside, rho)
+            x = x + rng.uniform(-0.05, 0.05, x.shape)
+            yield make("fcc_n%d_rho%g" % (nside, rho), x, box[0], 0.8)
+    # clustered: small dense balls (radius 4, density 0.6) centred on a
+    # random subset of the sites of a cubic lattice of spacing 9 (balls one
+    # unit apart, more than dmin: each is placed on its own)
+    for nblob in (10, 20, 40, 80, 160):
+        m = int(math.ceil(nblob ** (1.0 / 3.0))) + 1
+        box_len = 9.0 * m
+        sites = np.stack(np.meshgrid(*[np.arange(m)] * 3, indexing="ij"), -1).reshape(-1, 3)
+        centres = (sites[rng.permutation(len(sites))[:nblob]] + 0.5) * 9.0
+        target = int(round(0.6 * 4.0 / 3.0 * math.pi * 4.0 ** 3))
+        pts = np.concatenate([_rsa(c, 4.0, box_len, target, dmin, rng, inside=True, min_batch=2000) for c in centres])
+        yield make("blobs_%d" % nblob, _with_vapour(pts, box_len, 0.005, dmin, rng), box_len, 1.0)
+    # a dense fcc slab of width w (density 0.8) in a gas of density 0.02
+    for w in (5.0, 10.0, 20.0):
+        x, box = fcc_lattice(24, 0.8)
+        box_len = box[0]
+        x = x[np.abs(x[:, 0] - 0.5 * box_len) < 0.5 * w]
+        yield make("slab_w%g" % w, _with_vapour(x, box_len, 0.02, dmin, rng), box_len, 1.0)
+    # fcc balls (density 0.8) in a dilute vapour
+    for box_len, radius in ((60.0, 8.0), (60.0, 15.0), (100.0, 15.0), (100.0, 25.0), (150.0, 30.0)):
+        ncell = int(math.ceil(2 * radius / (4.0 / 0.8) ** (1.0 / 3.0))) + 1
+        x, box = fcc_lattice(ncell, 0.8)
+        x = x - 0.5 * box[0] + 0.5 * box_len
+        x = x[np.linalg.norm(x - 0.5 * box_len, axis=1) < radius]
+        yield make("ball_L%g_r%g" % (box_len, radius), _with_vapour(x, box_len, 0.005, dmin, rng), box_len, 3.0)
+    # an almost empty box
+    x = _rsa(np.full(3, 20.0), 0.0, 40.0, 50, dmin, rng, inside=False)
+    yield make("empty_L40", x, 40.0, 1.0)
