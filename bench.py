@@ -560,7 +560,7 @@ def main():
     ap.add_argument("--csf", type=float, default=1.0, help="with --method: cell size factor (1.0 or 0.5)")
     ap.add_argument("--trial-steps", type=int, default=5)
     ap.add_argument("--probe-steps", type=int, default=2)
-    ap.add_argument("--strategy", default="expert", choices=["full", "predictive", "expert", "forest"],
+    ap.add_argument("--strategy", default="forest", choices=["full", "predictive", "expert", "forest"],
                     help="tuning strategy of the headline run (the others of expert/full/forest are reported beside it)")
     ap.add_argument("--fixed-steps", type=int, default=-1, help="steps per fixed configuration (-1: same as --steps)")
     ap.add_argument("--profile-steps", type=int, default=60)
