@@ -458,12 +458,15 @@ def run_ours(args):
         th = np.zeros(n, np.int32)
         xo = np.empty_like(xh)
         vo = np.empty_like(vh)
+        model = lj_forest.load() if args.tune and args.strategy == "forest" else None
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
         hp = lj.make_params(sc["box"], skin=sc["skin"], dt=sc["dt"], use_graphs=not args.eager)
         h2 = lj.ljsel_create(hp, n, xh, vh, th, stream.cuda_stream)
         done2 = 0
+        if model is not None:
+            lj.ljsel_set_forest(h2, model)
         if args.tune:
             _, r2 = lj.ljsel_autotune(h2, strategy=args.strategy, trial_steps=args.trial_steps,
                                       probe_steps=args.probe_steps, probe_factor=2.0)
