@@ -106,3 +106,31 @@ def test_shipped_model_is_reproducible_from_shipped_data():
     # every record's class is its cheapest configuration
     for r, c in zip(forest.records(), y):
         assert r["costs"][c] == min(r["costs"].values())
+
+
+def test_training_scenarios_are_physical_inputs():
+    """The forest's training scenarios (input generators only): every particle
+    inside its box, no two closer than the 0.9 spacing outside the jittered
+    lattices (whose nearest neighbours sit at a/sqrt(2) - 0.1*sqrt(3) or
+    more), zero momentum and the drawn temperature exactly, boxes that admit
+    the minimum image at the scenario's skin, skins cycling 0.1 ... 0.5."""
+    from scipy.spatial import cKDTree
+
+    from paper_2505_03438_gb300 import scenarios
+    seen = []
+    for sc in scenarios.training_scenarios():
+        x, v, L = sc["x"], sc["v"], sc["box"][0]
+        n = len(x)
+        assert (x >= 0).all() and (x < L).all(), sc["name"]
+        assert L >= 2 * (2.5 + sc["skin"]) * (1 + 1 / 1024), sc["name"]
+        if n > 1:
+            d, _ = cKDTree(x, boxsize=L).query(x, k=2)
+            floor = 0.9 if not sc["name"].startswith("fcc") else 0.8
+            assert d[:, 1].min() >= floor - 1e-9, (sc["name"], d[:, 1].min())
+            assert np.abs(v.sum(0)).max() < 1e-9 * n, sc["name"]
+            assert abs((v * v).sum() / (3 * n - 3) - sc["temperature"]) < 1e-9, sc["name"]
+        seen.append((sc["name"], sc["skin"]))
+    assert len(seen) == 42
+    assert [s for _, s in seen[:10]] == [0.1, 0.2, 0.3, 0.4, 0.5] * 2
+    # the benchmark workloads are not among them
+    assert not any(nm.startswith("fcc_n64") or nm.startswith("heated") for nm, _ in seen)
