@@ -49,8 +49,10 @@ def _case(size):
 
 @pytest.mark.parametrize("precision", [1, 0], ids=["fp64", "fp32"])
 @pytest.mark.parametrize("size,cfg", [("small", None), ("full", None), ("small", dict(method="LC")),
-                                      ("full", dict(method="LC")), ("small", dict(method="VL", newton3=True))],
-                         ids=["small-rows", "full-rows", "small-cells", "full-cells", "small-n3l-cells"])
+                                      ("full", dict(method="LC")), ("small", dict(method="VL", newton3=True)),
+                                      ("small", dict(method="VL", csf=0.5)), ("small", dict(method="LC", csf=0.5))],
+                         ids=["small-rows", "full-rows", "small-cells", "full-cells", "small-n3l-cells",
+                              "small-rows-csf0.5", "small-cells-csf0.5"])
 def test_force_vjp_matches_oracle(size, cfg, precision):
     """Verlet-list rows (VL without N3L) and the cell traversal (every other
     configuration) give the same VJP as the oracle."""
