@@ -119,7 +119,9 @@ typedef struct ljsel_stats {
     double nbins;
     double nempty;
     double skin;
-    double threads;            /* resident GPU threads of the force launch     */
+    double threads;            /* threads the GPU keeps resident (SMs x
+                                  threads per SM): the device's parallelism,
+                                  as the paper's thread count is the run's    */
 } ljsel_stats;
 
 /* Counters since creation (host-side copies, refreshed by calls that

@@ -662,9 +662,14 @@ ljsel_status ljsel_get_stats(ljsel_system h, ljsel_stats *st) {
     st->nbins = (double)nbins;
     st->nempty = (double)nempty;
     st->skin = s->params.skin;
-    const ljsel_config &c = s->cfg;
-    st->threads = c.method == LJSEL_METHOD_CLUSTER ? (double)s->ncl_cap * c.threads_per_unit
-                                                   : (double)s->n * std::max(1, c.threads_per_unit);
+    // the counterpart of the paper's thread count: the threads the GPU keeps
+    // resident (SMs x threads per SM), a property of the device, not of the
+    // configuration in use
+    int dev = 0, per_sm = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    st->threads = (double)nsm * (double)per_sm;
     return LJSEL_OK;
 }
 
