@@ -149,7 +149,9 @@ typedef struct ljsel_tuner_opts {
                                   forest (the forest installed with
                                   ljsel_set_forest ranks its configurations
                                   from the Sec. 4 statistics; the forest_top
-                                  most probable are trialled)                 */
+                                  most probable are trialled; with forest_top
+                                  1 and the first choice already in use, the
+                                  phase keeps it without a trial)             */
     int32_t trial_steps;       /* steps per trial (>= 1); a trial first
                                   rebuilds, then advances trial_steps steps   */
     double predict_factor;     /* predictive: trial configs predicted within

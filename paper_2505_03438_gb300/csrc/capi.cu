@@ -623,10 +623,16 @@ ljsel_status ljsel_get_stats(ljsel_system h, ljsel_stats *st) {
         nbins *= g.nb[d];
     }
     const size_t nbytes = (size_t)s->n * 3 * sizeof(double);
-    Buf tmp;
-    TRY(tmp.ensure(nbytes + (size_t)nbins * 4));
-    double *dpos = (double *)tmp.ptr;
-    int *counts = (int *)((char *)tmp.ptr + nbytes);
+    TRY(s->b_stats.ensure(nbytes + (size_t)nbins * 4));
+    if (s->h_stats_cap < (size_t)nbins) {
+        if (s->h_stats) cudaFreeHost(s->h_stats);
+        s->h_stats = nullptr;
+        s->h_stats_cap = 0;
+        CK(cudaMallocHost((void **)&s->h_stats, (size_t)nbins * 4));
+        s->h_stats_cap = (size_t)nbins;
+    }
+    double *dpos = (double *)s->b_stats.ptr;
+    int *counts = (int *)((char *)s->b_stats.ptr + nbytes);
     ljsel_status rs = dispatch(s, [&](auto z) -> ljsel_status {
         using R = decltype(z);
         Dev<R> S;
@@ -634,14 +640,13 @@ ljsel_status ljsel_get_stats(ljsel_system h, ljsel_stats *st) {
         launch_export_state(S, dpos, nullptr, 1, s->stream);
         return LJSEL_OK;
     });
-    if (rs != LJSEL_OK) { tmp.release(); return rs; }
-    cudaMemsetAsync(counts, 0, nbins * 4, s->stream);
+    if (rs != LJSEL_OK) return rs;
+    CK(cudaMemsetAsync(counts, 0, nbins * 4, s->stream));
     k_bin_counts<<<div_up(s->n, 256), 256, 0, s->stream>>>(dpos, s->n, g, counts);
-    std::vector<int> hc(nbins);
-    cudaMemcpyAsync(hc.data(), counts, nbins * 4, cudaMemcpyDeviceToHost, s->stream);
-    cudaError_t e = cudaStreamSynchronize(s->stream);
-    tmp.release();
-    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return LJSEL_ERR_CUDA; }
+    CK(cudaGetLastError());
+    const int *hc = s->h_stats;
+    CK(cudaMemcpyAsync(s->h_stats, counts, nbins * 4, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
     const double mean = (double)s->n / (double)nbins;
     double var = 0;
     int mx = 0;
@@ -653,8 +658,28 @@ ljsel_status ljsel_get_stats(ljsel_system h, ljsel_stats *st) {
         nempty += hc[b] == 0;
     }
     var /= (double)nbins;
-    std::sort(hc.begin(), hc.end());
-    double median = (nbins % 2) ? hc[nbins / 2] : 0.5 * ((double)hc[nbins / 2 - 1] + (double)hc[nbins / 2]);
+    // median: the counts are small integers, so their sorted order is read
+    // off a histogram of the values instead of sorting the bins
+    // (a collapse into a few bins with millions each takes a selection on a
+    // copy instead)
+    std::vector<long long> hist(mx <= (1 << 22) ? (size_t)mx + 1 : 0, 0);
+    std::vector<int> copy;
+    if (hist.empty()) copy.assign(hc, hc + nbins);
+    else
+        for (long long b = 0; b < nbins; ++b) ++hist[hc[b]];
+    auto kth = [&](long long k) {  // value of rank k (0-based) in ascending order
+        if (hist.empty()) {
+            std::nth_element(copy.begin(), copy.begin() + k, copy.end());
+            return copy[k];
+        }
+        long long acc = 0;
+        for (int v = 0; v <= mx; ++v) {
+            acc += hist[v];
+            if (acc > k) return v;
+        }
+        return mx;
+    };
+    const double median = (nbins % 2) ? (double)kth(nbins / 2) : 0.5 * ((double)kth(nbins / 2 - 1) + (double)kth(nbins / 2));
     st->mean = mean;
     st->rel_std = mean > 0 ? std::sqrt(var) / mean : 0.0;
     st->median = median;
@@ -867,6 +892,24 @@ ljsel_status ljsel_autotune(ljsel_system h, const ljsel_tuner_opts *opts, ljsel_
         }
         if (!taken) trial[rank[0]] = 1;  // everything blacklisted: keep the forest's first choice
         expert_x = proba[rank[0]];
+        // one suggestion, and it is the configuration in use: nothing to
+        // decide, so the phase keeps it without a trial
+        if (top == 1 && same_cfg(cands[rank[0]], s->cfg)) {
+            ljsel_tuner_report r{};
+            s->tuner_phase += 1;
+            r.phase = s->tuner_phase;
+            r.chosen_index = rank[0];
+            const auto &hs = ent[rank[0]]->history;
+            r.chosen_cost_ms = hs.empty() ? 0.0 : hs.back().second;
+            r.expert_input = expert_x;
+            r.phase_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            s->tuned_stats = st_now;
+            s->have_tuned_stats = true;
+            s->last_report = r;
+            if (chosen) *chosen = s->cfg;
+            if (report) *report = r;
+            return LJSEL_OK;
+        }
     } else if (opts->strategy == 1) {
         const int nc = (int)cands.size();
         std::vector<int32_t> hn(nc), hp(2 * nc, 0), lt(nc), bl(nc), tr(nc);

@@ -141,6 +141,7 @@ System::~System() {
     drop_graph();
     for (Buf *b : all_bufs()) b->release();
     if (h_ctrl) cudaFreeHost(h_ctrl);
+    if (h_stats) cudaFreeHost(h_stats);
     if (ev_a) cudaEventDestroy(ev_a);
     if (ev_b) cudaEventDestroy(ev_b);
     if (cap_stream) cudaStreamDestroy(cap_stream);
@@ -151,7 +152,7 @@ std::vector<Buf *> System::all_bufs() {
             &b_xref, &b_force, &b_cell_count, &b_cell_start, &b_clcell_start, &b_cell_of, &b_slot_of, &b_key_of,
             &b_tmp_idx, &b_tmp_key, &b_cell_sorted, &b_scan, &b_nl, &b_nl_count, &b_strips, &b_nstrips, &b_cl_first, &b_cl_count,
             &b_cl_cell, &b_cl_lo, &b_cl_hi, &b_cp, &b_cp_count, &b_ncl, &b_ctrl, &b_io,
-            &b_adj_cot, &b_adj_x, &b_adj_v, &b_adj_theta, &b_ckpt, &b_seg};
+            &b_adj_cot, &b_adj_x, &b_adj_v, &b_adj_theta, &b_ckpt, &b_seg, &b_stats};
 }
 
 void System::drop_graph() {

@@ -85,6 +85,11 @@ struct System {
         ljsel_params params{};
     } rollout;
     Ctrl *h_ctrl = nullptr;  // pinned mirror
+    // live statistics: positions and bin counts on the device, the counts'
+    // pinned host copy (kept between calls: a tuning phase reads them)
+    Buf b_stats;
+    int *h_stats = nullptr;
+    size_t h_stats_cap = 0;
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     // step graphs, one per (configuration, device layout); gexec is the
     // current configuration's

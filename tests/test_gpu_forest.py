@@ -30,17 +30,29 @@ def test_forest_strategy_trials_the_forests_first_choices():
     assert e.value.status == 8  # LJSEL_ERR_STATE: no forest installed
     m = forest.load()
     s.set_forest(m)
-    for phase, top in enumerate((1, 3, 2)):
+    trialled = kept = 0
+    # two single-suggestion phases in a row: the second finds the first's
+    # choice in use (four steps barely move the statistics) and keeps it
+    for phase, top in enumerate((1, 1, 3, 2)):
         st = s.stats()
         p = forest.predict_proba(m, [st[k] for k in forest.FEATURES])
         expect = [m["classes"][k] for k in np.argsort(-p, kind="stable")[:top]]
+        before = s.config().name()
         c, rep = s.autotune(strategy="forest", trial_steps=4, forest_top=top)
-        assert rep["ntrialled"] == top and rep["expert_input"] == p.max()
+        assert rep["expert_input"] == p.max() and rep["phase"] == phase + 1
         costs = {k: v for k, (v, ph) in lj.ljsel_tuner_costs(s.h).items() if ph == phase}
+        if top == 1 and expect[0] == before:
+            # the single suggestion is the configuration in use: kept, no trial
+            assert rep["ntrialled"] == 0 and not costs and c.name() == before == s.config().name()
+            kept += 1
+            continue
+        assert rep["ntrialled"] == top
+        trialled += top
         assert sorted(costs) == sorted(expect)
         assert c.name() == min(costs, key=costs.get) and s.config().name() == c.name()
+    assert kept >= 1
     nsteps = s.counters()["steps"]
-    assert nsteps == 4 * (1 + 3 + 2)
+    assert nsteps == 4 * trialled
     x, v = s.state()
     xo, vo, *_ = oracle.verlet_run(sc["x"], sc["v"], None, [1.0], _orc_params(sc), sc["dt"], nsteps)
     assert np.abs(_wrapdiff(x, xo, sc["box"][0])).max() < 1e-9
