@@ -261,11 +261,15 @@ template <typename R> __global__ void k_bsortgather(BDev<R> S) {
 
 // Verlet list of each particle (thread per slot): every j of the 27 stencil
 // cells of its replica (periodic images of the replica's box) within the
-// list radius.  Row layout as for a single system: entries without an image
-// from the front in 16-byte chunks of four (the last padded with the
-// sentinel slot ntot), entries with an image (j | code << 27) from the back;
-// nl_count = front count | back count << 16.
-template <typename R> __global__ void k_bvl_build(BDev<R> S) {
+// list radius.  As for a single system, each (y, z) row of the stencil is
+// one run of consecutive slots (cells cx-1 .. cx+1, split only at a periodic
+// x edge of the replica), tested four candidates at a time into a 32-bit
+// mask per block of 32; only set bits are appended, in slot order (the order
+// of a cell-by-cell walk).  Row layout as for a single system: entries
+// without an image from the front in 16-byte chunks of four (the last
+// padded with the sentinel slot ntot), entries with an image (j | code << 27)
+// from the back; nl_count = front count | back count << 16.
+template <typename R> __global__ void __launch_bounds__(128) k_bvl_build(BDev<R> S) {
     Ctrl *C = S.ctrl;
     if (!C->rebuild_now) return;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -274,8 +278,9 @@ template <typename R> __global__ void k_bvl_build(BDev<R> S) {
     const V4<R> *P = S.pos[C->pos_par];
     const RepInfo<R> &I = S.rep[S.rep_of[q]];
     const V4<R> pi = P[q];
+    const int nx = I.nc[0], ny = I.nc[1], nz = I.nc[2];
     const int lc = S.cell_sorted[q] - I.cell_off;
-    const int cx = lc % I.nc[0], cy = (lc / I.nc[0]) % I.nc[1], cz = lc / (I.nc[0] * I.nc[1]);
+    const int cx = lc % nx, cy = (lc / nx) % ny, cz = lc / (nx * ny);
     const int cap = S.nl_cap;
     uint32_t *row = S.nl + (size_t)q * cap;
     uint4 *row4 = reinterpret_cast<uint4 *>(row);
@@ -283,29 +288,54 @@ template <typename R> __global__ void k_bvl_build(BDev<R> S) {
     int nf = 0, nb = 0;
     for (int oz = -1; oz <= 1; ++oz) {
         int wz, sz;
-        wrap_cell(cz, oz, I.nc[2], wz, sz);
+        wrap_cell(cz, oz, nz, wz, sz);
         for (int oy = -1; oy <= 1; ++oy) {
             int wy, sy;
-            wrap_cell(cy, oy, I.nc[1], wy, sy);
-            for (int ox = -1; ox <= 1; ++ox) {
-                int wx, sx;
-                wrap_cell(cx, ox, I.nc[0], wx, sx);
-                const int cc = I.cell_off + (wz * I.nc[1] + wy) * I.nc[0] + wx;
+            wrap_cell(cy, oy, ny, wy, sy);
+            const int rowc = I.cell_off + (wz * ny + wy) * nx;
+            // cells cx-1 .. cx+1 in unwrapped coordinates: left of the box
+            // (image -1), inside it, right of it (image +1)
+            for (int sx = -1; sx <= 1; ++sx) {
+                const int a = sx < 0 ? cx - 1 : (sx == 0 ? max(cx - 1, 0) : max(cx - 1, nx));
+                const int b = sx < 0 ? min(cx + 1, -1) : (sx == 0 ? min(cx + 1, nx - 1) : cx + 1);
+                if (a > b) continue;
+                const int jb = S.cell_start[rowc + a - sx * nx], je = S.cell_start[rowc + b - sx * nx + 1];
                 const uint32_t code = encode_image(sx, sy, sz);
-                const R shx = (R)sx * I.box[0], shy = (R)sy * I.box[1], shz = (R)sz * I.box[2];
-                const int jb = S.cell_start[cc], je = S.cell_start[cc + 1];
-                for (int j = jb; j < je; ++j) {
-                    if (code == 0 && j == q) continue;
-                    const V4<R> pj = P[j];
-                    const R dx = pi.x - (pj.x + shx), dy = pi.y - (pj.y + shy), dz = pi.z - (pj.z + shz);
-                    if (!(dx * dx + dy * dy + dz * dz < S.rlist2)) continue;
-                    if (code == 0) {
-                        b3 = b2; b2 = b1; b1 = b0; b0 = (uint32_t)j;
-                        ++nf;
-                        if ((nf & 3) == 0 && nf + nb <= cap) row4[(nf >> 2) - 1] = make_uint4(b0, b1, b2, b3);
-                    } else {
-                        if (((nf + 4) & ~3) + nb < cap) row[cap - 1 - nb] = (uint32_t)j | (code << JBITS);
-                        ++nb;
+                const bool self = code == 0 && jb <= q && q < je;
+                const R xs = pi.x - (R)sx * I.box[0], ys = pi.y - (R)sy * I.box[1], zs = pi.z - (R)sz * I.box[2];
+                for (int j0 = jb; j0 < je; j0 += 32) {
+                    const int m = min(32, je - j0);
+                    uint32_t mask = 0;
+                    int t = 0;
+                    for (; t + 4 <= m; t += 4) {
+                        const int j = j0 + t;
+                        const V4<R> q0 = ldpos(P, j), q1 = ldpos(P, j + 1), q2 = ldpos(P, j + 2), q3 = ldpos(P, j + 3);
+                        const uint32_t bits = (uint32_t)(r2_of(xs - q0.x, ys - q0.y, zs - q0.z) < S.rlist2) |
+                                              ((uint32_t)(r2_of(xs - q1.x, ys - q1.y, zs - q1.z) < S.rlist2) << 1) |
+                                              ((uint32_t)(r2_of(xs - q2.x, ys - q2.y, zs - q2.z) < S.rlist2) << 2) |
+                                              ((uint32_t)(r2_of(xs - q3.x, ys - q3.y, zs - q3.z) < S.rlist2) << 3);
+                        mask |= bits << t;
+                    }
+                    for (; t < m; ++t) {
+                        const V4<R> qq = ldpos(P, j0 + t);
+                        mask |= (uint32_t)(r2_of(xs - qq.x, ys - qq.y, zs - qq.z) < S.rlist2) << t;
+                    }
+                    if (self) {  // drop j == q
+                        const int rel = q - j0;
+                        if (rel >= 0 && rel < 32) mask &= ~(1u << rel);
+                    }
+                    while (mask) {
+                        const int bit = __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        const uint32_t j = (uint32_t)(j0 + bit);
+                        if (code == 0) {
+                            b3 = b2; b2 = b1; b1 = b0; b0 = j;
+                            ++nf;
+                            if ((nf & 3) == 0 && nf + nb <= cap) row4[(nf >> 2) - 1] = make_uint4(b0, b1, b2, b3);
+                        } else {
+                            if (((nf + 4) & ~3) + nb < cap) row[cap - 1 - nb] = j | (code << JBITS);
+                            ++nb;
+                        }
                     }
                 }
             }
