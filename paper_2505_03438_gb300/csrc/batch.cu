@@ -209,14 +209,16 @@ template <typename R> __global__ void k_bscatter(BDev<R> S) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= S.ntot) return;
     if (!S.rep_do[S.rep_of[g]]) return;
-    const int dst = S.cell_start[S.cell_of[g]] + S.slot_of[g];
+    const int cell = S.cell_of[g];
+    const int dst = S.cell_start[cell] + S.slot_of[g];
     S.tmp_idx[dst] = g;
     S.tmp_key[dst] = S.id[C->state_par][g];
+    S.cell_sorted[dst] = cell;  // the slot's cell: its final occupant is in the same cell
 }
 
-// One warp per cell: order the cell's particles by input index and gather
-// their state into the final slots of the other state buffer.
-template <typename R> __device__ __forceinline__ void bgather(const BDev<R> &S, int sp, int pp, int q, int p, int cell) {
+// Gather one particle's state into its final slot q of the other state
+// buffer (the slot's cell was recorded by the scatter).
+template <typename R> __device__ __forceinline__ void bgather(const BDev<R> &S, int sp, int pp, int q, int p) {
     const int n = S.ntot;
     const double *X = S.x[sp], *V = S.v[sp];
     double *Xn = S.x[sp ^ 1], *Vn = S.v[sp ^ 1];
@@ -227,36 +229,33 @@ template <typename R> __device__ __forceinline__ void bgather(const BDev<R> &S, 
     const V4<R> w = make_pos((R)x0, (R)x1, (R)x2, 0);
     S.pos[pp][q] = w;
     S.xref[q] = w;
-    S.cell_sorted[q] = cell;
 }
 
+// One thread per slot.  A replica not rebuilt keeps its slots: its state is
+// carried over to the buffer that becomes current.  In a rebuilt replica the
+// slot holds (in scattered order) an element of some cell; its rank among
+// the keys (input indices) of that cell is its final place in the cell.
 template <typename R> __global__ void k_bsortgather(BDev<R> S) {
     Ctrl *C = S.ctrl;
     if (!C->rebuild_now) return;
-    const int lane = threadIdx.x & 31;
-    const int cell = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (cell >= S.ncell) return;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= S.ntot) return;
     const int sp = C->state_par, pp = C->pos_par;
-    const int start = S.cell_start[cell], m = S.cell_start[cell + 1] - start;
-    if (!S.rep_do[S.cell_rep[cell]]) {
-        // a replica not rebuilt keeps its slots: carry its state over to the
-        // buffer that becomes current
+    if (!S.rep_do[S.rep_of[e]]) {
         const int n = S.ntot;
-        for (int q = start + lane; q < start + m; q += 32) {
-            for (int d = 0; d < 3; ++d) {
-                S.x[sp ^ 1][d * n + q] = S.x[sp][d * n + q];
-                S.v[sp ^ 1][d * n + q] = S.v[sp][d * n + q];
-            }
-            S.id[sp ^ 1][q] = S.id[sp][q];
+        for (int d = 0; d < 3; ++d) {
+            S.x[sp ^ 1][d * n + e] = S.x[sp][d * n + e];
+            S.v[sp ^ 1][d * n + e] = S.v[sp][d * n + e];
         }
+        S.id[sp ^ 1][e] = S.id[sp][e];
         return;
     }
-    for (int e = lane; e < ((m + 31) & ~31); e += 32) {
-        const int key = e < m ? S.tmp_key[start + e] : 0x7fffffff;
-        int rank = 0;
-        for (int f = 0; f < m; ++f) rank += S.tmp_key[start + f] < key ? 1 : 0;
-        if (e < m) bgather(S, sp, pp, start + rank, S.tmp_idx[start + e], cell);
-    }
+    const int cell = S.cell_sorted[e];
+    const int start = S.cell_start[cell], m = S.cell_start[cell + 1] - start;
+    const int key = S.tmp_key[e];
+    int rank = 0;
+    for (int f = 0; f < m; ++f) rank += S.tmp_key[start + f] < key ? 1 : 0;
+    bgather(S, sp, pp, start + rank, S.tmp_idx[e]);
 }
 
 // Verlet list of each particle (thread per slot): every j of the 27 stencil
@@ -664,7 +663,7 @@ struct ljsel_batch_s {
         k_bbin<R><<<div_up(ntot, 256), 256, 0, st>>>(S);
         k_bscan_rep<R><<<nrep, SCAN_BLOCK, 0, st>>>(S);
         k_bscatter<R><<<div_up(ntot, 256), 256, 0, st>>>(S);
-        k_bsortgather<R><<<div_up((long long)ncell * 32, 256), 256, 0, st>>>(S);
+        k_bsortgather<R><<<div_up(ntot, 256), 256, 0, st>>>(S);
         k_bvl_build<R><<<div_up(ntot, 128), 128, 0, st>>>(S);
         launch_rebuild_finish(S.ctrl, st);
     }
