@@ -272,6 +272,13 @@ def test_live_statistics(lj):
         ref = oracle.bin_stats(x, sc["box"], 2.5 + sc["skin"])
         for k in ("mean", "rel_std", "median", "max", "nbins", "nempty"):
             assert abs(st[k] - ref[k]) <= 1e-12 * max(1.0, abs(ref[k])), (k, st[k], ref[k])
+        # the thread count: the device's resident threads, whatever the configuration
+        import torch
+        props = torch.cuda.get_device_properties(0)
+        assert st["threads"] == props.multi_processor_count * props.max_threads_per_multi_processor
+        assert st["skin"] == sc["skin"]
+        s.set_config(method="VL", threads_per_unit=4)
+        assert s.stats()["threads"] == st["threads"]
         s.close()
 
 
