@@ -332,7 +332,7 @@ template <typename R> __global__ void __launch_bounds__(128) k_bvl_build(BDev<R>
                             ++nf;
                             if ((nf & 3) == 0 && nf + nb <= cap) row4[(nf >> 2) - 1] = make_uint4(b0, b1, b2, b3);
                         } else {
-                            if (((nf + 4) & ~3) + nb < cap) row[cap - 1 - nb] = j | (code << JBITS);
+                            if (nb < cap) row[cap - 1 - nb] = j | (code << JBITS);  // inside the row (see the single-system build)
                             ++nb;
                         }
                     }

@@ -272,7 +272,10 @@ __global__ void __launch_bounds__(VL_BUILD_THREADS, VL_BUILD_MIN_BLOCKS) k_vl_bu
             ++nf;
             if ((nf & 3) == 0 && nf + nb <= cap) row[(nf >> 2) - 1] = make_uint4(b0, b1, b2, b3);
         } else {
-            if (nf + nb < cap && ((nf + 4) & ~3) + nb < cap) rowp[cap - 1 - nb] = (uint32_t)j | (code << JBITS);
+            // an image entry only has to stay inside the row: if the row's
+            // final length fits, the back cannot meet the front; if not, the
+            // row is discarded
+            if (nb < cap) rowp[cap - 1 - nb] = (uint32_t)j | (code << JBITS);
             ++nb;
         }
     };

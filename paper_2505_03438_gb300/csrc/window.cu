@@ -288,7 +288,9 @@ __global__ void __launch_bounds__(WTHREADS) k_vlw_build(Dev<R> S) {
                     ++nf;
                     if ((nf & 7) == 0 && nf + nb <= hcap) half[(nf >> 3) - 1] = make_uint4(pk.w0, pk.w1, pk.w2, pk.w3);
                 } else {
-                    if (((nf + 8) & ~7) + nb < hcap) half16[hcap - 1 - nb] = (uint16_t)(slot | (code << 11));
+                    // inside the half row: if its final length fits, the back
+                    // cannot meet the front; if not, the row is discarded
+                    if (nb < hcap) half16[hcap - 1 - nb] = (uint16_t)(slot | (code << 11));
                     ++nb;
                 }
             };
