@@ -130,7 +130,8 @@ typedef struct ljsel_counters {
     int64_t steps;             /* Verlet steps taken                           */
     int64_t rebuilds;          /* neighbour-structure rebuilds                 */
     int64_t early_rebuilds;    /* rebuilds forced by the skin/2 displacement   */
-    int64_t list_entries;      /* entries of the current list (0 for LC)       */
+    int64_t list_entries;      /* entries kept by the last list build, summed
+                                  over all rows (0 for LC)                     */
     int64_t list_capacity;     /* allocated entries                            */
     int64_t nclusters;         /* i-clusters (CLUSTER)                         */
     int64_t ncells;            /* cells of the current grid                    */
@@ -138,6 +139,7 @@ typedef struct ljsel_counters {
     int64_t replica_rebuilds;  /* batches: replica rebuilds summed over all
                                   replicas (each rebuild event re-lists only
                                   the replicas that need it); 0 otherwise     */
+    int64_t longest_row;       /* longest list row of the last build          */
 } ljsel_counters;
 
 /* Autotuner options (Sec. 2.2.5 Full Search, Sec. 5.1 Predictive, Sec. 5.2
@@ -506,29 +508,34 @@ ljsel_status ljsel_batch_autotune(ljsel_batch b, int32_t trial_steps, int32_t nc
 ljsel_status ljsel_selftest_wait_timeout(int64_t polls);
 
 /* Allocation-free force evaluation.  The paper has no counterpart: this is
- * a service for callers that cannot allocate device memory -- code running
- * while a stream is captured into a CUDA graph, code inside a framework
- * whose allocator owns all device memory, or latency-critical loops that
- * must not enter the allocator.  It bins the particles into linked cells of
- * side >= max r_cut (no skin) and evaluates the library's FP32 LJ pair
- * arithmetic with the exact cutoff decision, using only a fixed 5.8 MB
- * static device array inside the library (held by every GPU that loads the
- * library until the process exits) and the caller's buffers.
- *   params: as for ljsel_create; precision must be 0.
+ * a service for callers that cannot allocate device memory -- code inside a
+ * framework whose allocator has reserved all device memory and forbids
+ * allocations behind its back, plug-ins running inside a host application
+ * that owns the device, or latency-critical loops that must not take the
+ * allocator's locks or the implicit synchronization of a free.  It bins the
+ * particles into linked cells of side >= max r_cut (no skin) and evaluates
+ * the library's FP32 LJ pair arithmetic with the exact cutoff decision,
+ * using only a fixed 5.8 MB static device array inside the library (held
+ * by every GPU that loads the library until the process exits) and the
+ * caller's buffers.
+ *   params: as for ljsel_create; precision must be 0; periodic box only.
  *   n: 1 .. 131072 particles; larger n, or a box needing more than 131072
- *      cells, returns LJSEL_ERR_CAPACITY.
+ *      cells, returns LJSEL_ERR_CAPACITY before any work is enqueued.
  *   pos: device, n x 3 doubles (wrapped into the box on the fly);
  *   types: device, n int32 in [0, ntypes) (NULL: all 0);
  *   forces: device, n x 3 doubles, written in input order;
  *   energy, virial: host doubles or NULL; when either is given the call
- *      synchronizes the stream.
+ *      reads them back and synchronizes the stream, so it returns
+ *      LJSEL_ERR_STATE (enqueuing nothing) when the stream is being
+ *      captured.
  *   stream: cudaStream_t or NULL.
- * The first call on a device resolves the address of the static array (with
- * that device current); make that first call before any stream capture.
- * All calls share the array and it keeps the last call's contents (each
- * call clears what must start at zero); calls whose GPU work overlaps (on
- * different streams or from different threads) race on it, so serialize
- * them.  Calls no cudaMalloc, cudaFree or other allocating routine.        */
+ * The first call in a CUDA context resolves the device address of the
+ * static array (with that device current) and caches it per context; make
+ * that first call before any stream capture.  All calls share the array and
+ * it keeps the last call's contents (each call clears what must start at
+ * zero); calls whose GPU work overlaps (on different streams or from
+ * different threads) race on it, so serialize them.  Calls no cudaMalloc,
+ * cudaFree or other allocating routine.                                   */
 ljsel_status ljsel_compute_forces_noalloc(const ljsel_params *params, int64_t n, const double *pos,
                                           const int32_t *types, double *forces, double *energy, double *virial,
                                           void *stream);

@@ -93,7 +93,7 @@ class ljsel_stats(ctypes.Structure):
 class ljsel_counters(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("steps", "rebuilds", "early_rebuilds", "list_entries",
                                                "list_capacity", "nclusters", "ncells", "capacity_retries",
-                                               "replica_rebuilds")]
+                                               "replica_rebuilds", "longest_row")]
 
 
 class ljsel_tuner_opts(ctypes.Structure):

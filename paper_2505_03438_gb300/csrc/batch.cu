@@ -1233,7 +1233,7 @@ ljsel_status ljsel_batch_get_counters(ljsel_batch b, ljsel_counters *c) {
     c->steps = b->h_ctrl->total_steps;
     c->rebuilds = b->h_ctrl->rebuilds;
     c->early_rebuilds = b->h_ctrl->early_rebuilds;
-    c->list_entries = b->h_ctrl->need_cap;
+    c->longest_row = b->h_ctrl->need_cap;
     c->list_capacity = (int64_t)b->nl_cap * b->ntot;
     c->ncells = b->ncell;
     c->capacity_retries = b->retries;

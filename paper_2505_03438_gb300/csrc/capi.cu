@@ -107,10 +107,13 @@ std::vector<ljsel_config> default_candidates(const System &s) {
     add(LJSEL_METHOD_VL, 1, 0, 2, 0.5, 2 * R);
     for (int n3 = 0; n3 <= 1; ++n3) add(LJSEL_METHOD_VLW, 1, n3, 1, 1.0, R);
     add(LJSEL_METHOD_VLW, 1, 0, 1, 1.0, 2 * R);
-    for (int M : {4, 8, 32}) {
-        for (int t = M; t <= 32; t *= 2) add(LJSEL_METHOD_CLUSTER, M, 0, t, 1.0, R);
-        add(LJSEL_METHOD_CLUSTER, M, 1, M, 1.0, R);
-    }
+    // i-clusters of M particles with union lists: T lanes per cluster
+    for (int t : {2, 4, 8}) add(LJSEL_METHOD_CLUSTER, 2, 0, t, 1.0, R);
+    for (int t : {4, 8, 16}) add(LJSEL_METHOD_CLUSTER, 4, 0, t, 1.0, R);
+    for (int t : {8, 16}) add(LJSEL_METHOD_CLUSTER, 8, 0, t, 1.0, R);
+    add(LJSEL_METHOD_CLUSTER, 2, 1, 4, 1.0, R);
+    add(LJSEL_METHOD_CLUSTER, 4, 1, 8, 1.0, R);
+    add(LJSEL_METHOD_CLUSTER, 8, 1, 8, 1.0, R);
     return v;
 }
 
@@ -710,13 +713,15 @@ ljsel_status ljsel_get_counters(ljsel_system h, ljsel_counters *c) {
     c->capacity_retries = s->capacity_retries;
     if (s->cfg.method == LJSEL_METHOD_VL || s->cfg.method == LJSEL_METHOD_VLW) {
         c->list_capacity = (int64_t)s->nl_cap * s->n;  // row-major, nl_cap per particle
-        c->list_entries = s->h_ctrl->need_cap;  // longest row of the last build
+        c->list_entries = s->h_ctrl->list_entries;
+        c->longest_row = s->h_ctrl->need_cap;
     } else if (s->cfg.method == LJSEL_METHOD_CLUSTER) {
         int ncl = 0;
         CK(cudaMemcpy(&ncl, s->b_ncl.ptr, 4, cudaMemcpyDeviceToHost));
         c->nclusters = ncl;
         c->list_capacity = (int64_t)s->cp_cap * ncl;
-        c->list_entries = s->h_ctrl->need_cap;
+        c->list_entries = s->h_ctrl->list_entries;
+        c->longest_row = s->h_ctrl->need_cap;
     }
     return LJSEL_OK;
 }

@@ -9,6 +9,7 @@
 // Integration is FP64: v += (dt/m) F, x += dt v, with the FP32 working copy
 // rounded from the FP64 position.
 #include "kernels.cuh"
+#include "update.cuh"
 
 namespace ljsel {
 
@@ -78,73 +79,6 @@ __device__ __forceinline__ void add_force(float4 *F, int j, float x, float y, fl
 }
 __device__ __forceinline__ void add_force(D4 *F, int j, double x, double y, double z) {
     atomicAdd(&F[j].x, x); atomicAdd(&F[j].y, y); atomicAdd(&F[j].z, z);
-}
-
-// FP64 block reduction of energy, virial and kinetic energy into Ctrl.
-__device__ __forceinline__ void block_sum3(double a, double b, double c, Ctrl *C) {
-    __shared__ double s[3][32];
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, o);
-        b += __shfl_down_sync(0xffffffffu, b, o);
-        c += __shfl_down_sync(0xffffffffu, c, o);
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    if (lane == 0) { s[0][warp] = a; s[1][warp] = b; s[2][warp] = c; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double x = 0, y = 0, z = 0;
-        for (int k = 0; k < nw; ++k) { x += s[0][k]; y += s[1][k]; z += s[2][k]; }
-        if (x != 0.0) atomicAdd(&C->epot, x);
-        if (y != 0.0) atomicAdd(&C->virial, y);
-        if (z != 0.0) atomicAdd(&C->ekin, z);
-    }
-}
-
-// Stormer-Verlet update of one particle (Sec. 2.1) in leapfrog form: the
-// stored velocity is at the half step (or, with `half`, at the integer step,
-// and the kick is dt/2).  v += (dt/m) F; x += dt v; the working copy is the
-// FP32 rounding of the FP64 position.  Returns |x - x_ref|^2 exceedance and
-// the kinetic energy at the integer step (EV).
-template <typename R, bool EV>
-__device__ __forceinline__ void integrate_one(const Dev<R> &S, int sp, int pp, int half, int i, int t, R fx, R fy,
-                                              R fz, double &ke, bool &exceeded, bool &bad) {
-    const int n = S.n;
-    double *X = S.x[sp];
-    double *V = S.v[sp];
-    R c = S.tab.inv_mass_dt[t];
-    if (half) c *= (R)0.5;
-    double vx = V[i], vy = V[n + i], vz = V[2 * n + i];
-    double dvx = (double)(c * fx), dvy = (double)(c * fy), dvz = (double)(c * fz);
-    if (EV) {
-        double h = half ? 0.0 : 0.5;
-        double ux = vx + h * (double)(S.tab.inv_mass_dt[t] * fx);
-        double uy = vy + h * (double)(S.tab.inv_mass_dt[t] * fy);
-        double uz = vz + h * (double)(S.tab.inv_mass_dt[t] * fz);
-        ke += S.tab.half_mass[t] * (ux * ux + uy * uy + uz * uz);
-    }
-    vx += dvx; vy += dvy; vz += dvz;
-    const double dt = S.tab.dt;
-    double x = fma(dt, vx, X[i]);
-    double y = fma(dt, vy, X[n + i]);
-    double z = fma(dt, vz, X[2 * n + i]);
-    // reflective walls: mirror a crossing back and reverse the velocity component
-    if (S.walls[0]) { if (x < 0.0) { x = -x; vx = -vx; } else if (x > S.boxd[0]) { x = 2.0 * S.boxd[0] - x; vx = -vx; } }
-    if (S.walls[1]) { if (y < 0.0) { y = -y; vy = -vy; } else if (y > S.boxd[1]) { y = 2.0 * S.boxd[1] - y; vy = -vy; } }
-    if (S.walls[2]) { if (z < 0.0) { z = -z; vz = -vz; } else if (z > S.boxd[2]) { z = 2.0 * S.boxd[2] - z; vz = -vz; } }
-    V[i] = vx; V[n + i] = vy; V[2 * n + i] = vz;
-    X[i] = x; X[n + i] = y; X[2 * n + i] = z;
-    V4<R> w = make_pos((R)x, (R)y, (R)z, t);
-    S.pos[pp ^ 1][i] = w;
-    V4<R> r = S.xref[i];
-    R ddx = w.x - r.x, ddy = w.y - r.y, ddz = w.z - r.z;
-    R d2 = ddx * ddx + ddy * ddy + ddz * ddz;
-    exceeded = exceeded || !(d2 < S.half_skin2);
-    bad = bad || !isfinite(fx + fy + fz);
-}
-
-__device__ __forceinline__ void report_flags(Ctrl *C, bool exceeded, bool bad) {
-    if (__any_sync(0xffffffffu, exceeded) && (threadIdx.x & 31) == 0) C->disp_exceeded = 1;
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) C->nonfinite = 1;
 }
 
 template <typename R>

@@ -106,7 +106,7 @@ struct Ctrl {
     int64_t rebuilds;
     int64_t early_rebuilds;
     int64_t need_cap;          // largest per-row list length required
-    int64_t list_entries;      // entries written by the last list build
+    int64_t list_entries;      // entries kept by the last list build (all rows)
     unsigned long long npairs; // pair-export counter
     int32_t scan_ticket;
     int32_t rebuild_all;       // batches: the next rebuild covers every replica
@@ -163,17 +163,15 @@ template <typename R> struct Dev {
     int4 *strips;
     int *nstrips;
     int strip_cap;
-    // clusters
+    // i-clusters and their lists
     int M;                // cluster size
     int ncl_cap;
     int *cl_first;        // [ncl] first sorted particle
     int *cl_count;        // [ncl]
     int *cl_cell;         // [ncl]
-    P4 *cl_lo, *cl_hi;    // bounding boxes
-    uint32_t *cp;         // ELL cluster-pair list, column-major over i-clusters
-    int *cp_count;
+    uint32_t *cp;         // cluster lists, row c at cp + c * cp_cap
+    int *cp_count;        // [ncl] front count | back count << 16
     int cp_cap;
-    int cp_stride;
     int *ncl_total;       // device scalar: clusters of the current build
     Ctrl *ctrl;
     PairTab<R> tab;
@@ -256,6 +254,18 @@ __device__ __forceinline__ void block_need_max(Ctrl *C, unsigned v) {
     if ((threadIdx.x & 31) == 0 && m) atomicMax(&s_need, m);
     __syncthreads();
     if (threadIdx.x == 0 && s_need) atomicMax(reinterpret_cast<unsigned long long *>(&C->need_cap), (unsigned long long)s_need);
+}
+
+// Entries kept by a list build, summed per block, then one atomicAdd on
+// Ctrl::list_entries.  Every thread of the block must make the call.
+__device__ __forceinline__ void block_add_entries(Ctrl *C, unsigned v) {
+    __shared__ unsigned long long s_sum;
+    if (threadIdx.x == 0) s_sum = 0ull;
+    __syncthreads();
+    const unsigned w = __reduce_add_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0 && w) atomicAdd(&s_sum, (unsigned long long)w);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_sum) atomicAdd(reinterpret_cast<unsigned long long *>(&C->list_entries), s_sum);
 }
 
 // Decides "r < r_c" for one pair exactly as the FP64 predicate does: in the

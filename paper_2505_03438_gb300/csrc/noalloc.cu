@@ -1,10 +1,10 @@
 // noalloc.cu -- a one-shot force evaluation that allocates no memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA stream is
-// being captured into a graph (allocation is not a capturable operation),
-// code inside a framework whose own allocator owns all device memory and
-// forbids outside allocations, and latency-critical loops that must not
-// take the allocator's locks or trigger an implicit synchronization.  For
+// Some callers cannot call cudaMalloc: code inside a framework whose own
+// allocator has reserved all device memory and forbids allocations behind
+// its back, plug-ins that run inside a host application that owns the
+// device, and latency-critical loops that must not take the allocator's
+// locks or trigger the implicit synchronization a cudaFree implies.  For
 // them, ljsel_compute_forces_noalloc bins the particles into linked cells
 // and evaluates the same FP32 LJ pair arithmetic as the library's
 // linked-cell kernel, with every intermediate array held in one file-scope
@@ -176,10 +176,44 @@ __global__ void __launch_bounds__(NA_THREADS) k_na_force(NaScratch *S, NaGrid g,
     }
 }
 
-// Device address of the scratch array, resolved once per device with that
-// device current (the host-side name is only a stand-in, not an address).
+// Device address of the scratch array, resolved with cudaGetSymbolAddress
+// once per CUDA context (the host-side name is only a stand-in, not an
+// address).  The cache is keyed by the context's unique id, so that a
+// context destroyed by cudaDeviceReset and created again resolves the
+// address anew instead of reusing a dangling one.  When the context id is
+// not available the address is resolved on every call.
 std::mutex g_na_mutex;
-NaScratch *g_na_addr[64] = {nullptr};
+struct NaSlot {
+    unsigned long long ctx_id = 0;
+    NaScratch *addr = nullptr;
+};
+NaSlot g_na_addr[64];
+
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+
+// Id of the current context through the driver entry points (0 if unknown).
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_cur = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_cur = (CtxGetCurrentFn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (CtxGetIdFn)f;
+    }
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_cur || !get_id || get_cur(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0ull;
+    return id;
+}
 
 }  // namespace
 }  // namespace ljsel
@@ -216,18 +250,33 @@ extern "C" ljsel_status ljsel_compute_forces_noalloc(const ljsel_params *params,
         g.box_lo[d] = (float)(params->box[d] - (double)g.box[d]);
         g.boxd[d] = params->box[d];
     }
+    cudaStream_t st_ = (cudaStream_t)stream;
+    if (energy || virial) {
+        // the sums are read back with a synchronize, which a stream being
+        // captured does not allow (it would invalidate the caller's capture)
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st_, &cs) != cudaSuccess) { set_error("invalid stream"); return LJSEL_ERR_ARG; }
+        if (cs != cudaStreamCaptureStatusNone) {
+            set_error("energy and virial are read back with a stream synchronize, which is not allowed while the "
+                      "stream is being captured: pass NULL for both");
+            return LJSEL_ERR_STATE;
+        }
+    }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { set_error("no current CUDA device"); return LJSEL_ERR_CUDA; }
     NaScratch *S = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_na_mutex);
-        if (!g_na_addr[dev]) {
+        const unsigned long long ctx = current_context_id();
+        NaSlot &slot = g_na_addr[dev];
+        if (!slot.addr || ctx == 0ull || slot.ctx_id != ctx) {
             void *p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess || !p) { set_error(std::string("cudaGetSymbolAddress failed: ") + cudaGetErrorString(e)); return LJSEL_ERR_CUDA; }
-            g_na_addr[dev] = (NaScratch *)p;
+            slot.addr = (NaScratch *)p;
+            slot.ctx_id = ctx;
         }
-        S = g_na_addr[dev];
+        S = slot.addr;
     }
     // the pair table of the library's FP32 path
     System tmp;
@@ -235,7 +284,6 @@ extern "C" ljsel_status ljsel_compute_forces_noalloc(const ljsel_params *params,
     tmp.n = (int)n;
     Dev<float> D;
     tmp.fill_dev(D);
-    cudaStream_t st_ = (cudaStream_t)stream;
     k_na_clear<<<div_up(g.ncell, 256) < 1024 ? div_up(g.ncell, 256) : 1024, 256, 0, st_>>>(S, g.ncell);
     k_na_bin<<<div_up(n, 256), 256, 0, st_>>>(S, g, pos);
     k_na_scan<<<1, NA_SCAN_THREADS, 0, st_>>>(S, g.ncell);

@@ -38,6 +38,7 @@ __global__ void k_bin(Dev<R> S, int ntiles) {
     if (p < ntiles) reinterpret_cast<unsigned long long *>(S.scan_partial)[p] = 0ull;
     if (p == 0) {
         C->need_cap = 0;
+        C->list_entries = 0;
         C->window_overflow = 0;
         if (S.nstrips) *S.nstrips = 0;
     }
@@ -352,116 +353,27 @@ __global__ void __launch_bounds__(VL_BUILD_THREADS, VL_BUILD_MIN_BLOCKS) k_vl_bu
         }
     }
     block_need_max(C, act ? (unsigned)need : 0u);
+    block_add_entries(C, (act && need <= cap) ? (unsigned)need : 0u);
 }
 
 // Clusters: each cell's segment is cut into chunks of M consecutive sorted
 // particles (the last may be shorter); one thread per cell writes its
-// clusters' extent and bounding box.
+// clusters' first particle, size and cell.
 template <typename R>
 __global__ void k_cluster_form(Dev<R> S) {
     Ctrl *C = S.ctrl;
     if (!C->rebuild_now) return;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= S.ncell) return;
-    const V4<R> *P = S.pos[C->pos_par];
     const int start = S.cell_start[c], m = S.cell_start[c + 1] - start;
     const int cl0 = S.clcell_start[c];
     for (int k = 0; k * S.M < m; ++k) {
-        int cl = cl0 + k;
+        const int cl = cl0 + k;
         if (cl >= S.ncl_cap) { C->overflow = 1; return; }
-        int first = start + k * S.M;
-        int cnt = min(S.M, m - k * S.M);
-        V4<R> lo = P[first], hi = lo;
-        for (int a = 1; a < cnt; ++a) {
-            V4<R> q = P[first + a];
-            lo.x = min(lo.x, q.x); lo.y = min(lo.y, q.y); lo.z = min(lo.z, q.z);
-            hi.x = max(hi.x, q.x); hi.y = max(hi.y, q.y); hi.z = max(hi.z, q.z);
-        }
-        S.cl_first[cl] = first;
-        S.cl_count[cl] = cnt;
+        S.cl_first[cl] = start + k * S.M;
+        S.cl_count[cl] = min(S.M, m - k * S.M);
         S.cl_cell[cl] = c;
-        S.cl_lo[cl] = lo;
-        S.cl_hi[cl] = hi;
     }
-}
-
-template <typename R>
-__device__ __forceinline__ R box_gap(R loi, R hii, R loj, R hij, int s, R L) {
-    R sh = s == 0 ? (R)0 : (s > 0 ? L : -L);
-    R a = (loj + sh) - hii;
-    R b = loi - (hij + sh);
-    R g = a > b ? a : b;
-    return g > (R)0 ? g : (R)0;
-}
-
-// Cluster-pair list row of i-cluster ci: j-clusters in the stencil cells
-// whose bounding boxes come closer than r_list and (M <= 8) that hold at
-// least one particle pair closer than r_list.  With N3L only cj > ci and the
-// cluster itself.
-template <typename R, bool N3L>
-__device__ __forceinline__ int cp_row(const Dev<R> &S, int ci, const V4<R> *P) {
-    const V4<R> loi = S.cl_lo[ci], hii = S.cl_hi[ci];
-    const int fi = S.cl_first[ci], ni = S.cl_count[ci];
-    const int c = S.cl_cell[ci];
-    const int cx = c % S.nc[0], cy = (c / S.nc[0]) % S.nc[1], cz = c / (S.nc[0] * S.nc[1]);
-    const int rch = S.reach;
-    int cnt = 0;
-    for (int oz = -rch; oz <= rch; ++oz) {
-        int wz, sz;
-        if (!stencil_cell(cz, oz, S.nc[2], S.walls[2], wz, sz)) continue;
-        for (int oy = -rch; oy <= rch; ++oy) {
-            int wy, sy;
-            if (!stencil_cell(cy, oy, S.nc[1], S.walls[1], wy, sy)) continue;
-            for (int ox = -rch; ox <= rch; ++ox) {
-                int wx, sx;
-                if (!stencil_cell(cx, ox, S.nc[0], S.walls[0], wx, sx)) continue;
-                int cc = (wz * S.nc[1] + wy) * S.nc[0] + wx;
-                uint32_t code = encode_image(sx, sy, sz);
-                int jb = S.clcell_start[cc], je = S.clcell_start[cc + 1];
-                for (int cj = jb; cj < je; ++cj) {
-                    if (N3L && (cj < ci || (cj == ci && code != 0))) continue;
-                    V4<R> loj = S.cl_lo[cj], hij = S.cl_hi[cj];
-                    R gx = box_gap(loi.x, hii.x, loj.x, hij.x, sx, S.box[0]);
-                    R gy = box_gap(loi.y, hii.y, loj.y, hij.y, sy, S.box[1]);
-                    R gz = box_gap(loi.z, hii.z, loj.z, hij.z, sz, S.box[2]);
-                    if (!(gx * gx + gy * gy + gz * gz < S.rlist2)) continue;
-                    bool keep = S.M > 8;
-                    if (!keep) {
-                        const int fj = S.cl_first[cj], nj = S.cl_count[cj];
-                        for (int a = 0; a < ni && !keep; ++a) {
-                            V4<R> pa = P[fi + a];
-                            for (int b = 0; b < nj; ++b) {
-                                if (cj == ci && code == 0 && a == b) continue;
-                                V4<R> pb = P[fj + b];
-                                R dx = image_dx(pa.x, pb.x, sx, S.box[0], S.box_lo[0]);
-                                R dy = image_dx(pa.y, pb.y, sy, S.box[1], S.box_lo[1]);
-                                R dz = image_dx(pa.z, pb.z, sz, S.box[2], S.box_lo[2]);
-                                if (r2_of(dx, dy, dz) < S.rlist2) { keep = true; break; }
-                            }
-                        }
-                    }
-                    if (!keep) continue;
-                    if (cnt < S.cp_cap) S.cp[(size_t)cnt * S.cp_stride + ci] = (uint32_t)cj | (code << JBITS);
-                    ++cnt;
-                }
-            }
-        }
-    }
-    return cnt;
-}
-template <typename R, bool N3L>
-__global__ void k_cp_build(Dev<R> S) {
-    Ctrl *C = S.ctrl;
-    if (!C->rebuild_now) return;
-    const int ci = blockIdx.x * blockDim.x + threadIdx.x;
-    const int ncl = *S.ncl_total;
-    const bool valid = ci < ncl && ci < S.ncl_cap;
-    const int cnt = valid ? cp_row<R, N3L>(S, ci, S.pos[C->pos_par]) : 0;
-    if (valid) {
-        S.cp_count[ci] = cnt < S.cp_cap ? cnt : S.cp_cap;
-        if (cnt > S.cp_cap) C->overflow = 1;
-    }
-    block_need_max(C, (unsigned)cnt);
 }
 
 __global__ void k_rebuild_finish(Ctrl *C) {
@@ -502,10 +414,6 @@ template <typename R> void launch_vl_build(const Dev<R> &S, bool n3l, cudaStream
 template <typename R> void launch_cluster_form(const Dev<R> &S, cudaStream_t st) {
     k_cluster_form<R><<<div_up(S.ncell, 128), 128, 0, st>>>(S);
 }
-template <typename R> void launch_cp_build(const Dev<R> &S, bool n3l, cudaStream_t st) {
-    if (n3l) k_cp_build<R, true><<<div_up(S.ncl_cap, 128), 128, 0, st>>>(S);
-    else k_cp_build<R, false><<<div_up(S.ncl_cap, 128), 128, 0, st>>>(S);
-}
 void launch_rebuild_finish(Ctrl *C, cudaStream_t st) { k_rebuild_finish<<<1, 1, 0, st>>>(C); }
 
 #define INST(R)                                                                 \
@@ -514,8 +422,7 @@ void launch_rebuild_finish(Ctrl *C, cudaStream_t st) { k_rebuild_finish<<<1, 1, 
     template void launch_scatter<R>(const Dev<R> &, cudaStream_t);              \
     template void launch_sortgather<R>(const Dev<R> &, cudaStream_t);           \
     template void launch_vl_build<R>(const Dev<R> &, bool, cudaStream_t);       \
-    template void launch_cluster_form<R>(const Dev<R> &, cudaStream_t);         \
-    template void launch_cp_build<R>(const Dev<R> &, bool, cudaStream_t);
+    template void launch_cluster_form<R>(const Dev<R> &, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

@@ -114,9 +114,8 @@ ljsel_status validate_config(const System &s, const ljsel_config *c) {
         if (t != 1 && t != 2 && t != 4 && t != 8 && t != 16 && t != 32) { set_error("VL threads_per_unit must be a power of two <= 32"); return LJSEL_ERR_UNSUPPORTED; }
     } else if (c->method == LJSEL_METHOD_CLUSTER) {
         const int M = c->cluster_size;
-        if (M != 4 && M != 8 && M != 32) { set_error("cluster_size must be 4, 8 or 32"); return LJSEL_ERR_UNSUPPORTED; }
+        if (M != 2 && M != 4 && M != 8) { set_error("cluster_size must be 2, 4 or 8"); return LJSEL_ERR_UNSUPPORTED; }
         if (t < M || t > 32 || (t & (t - 1)) != 0) { set_error("CLUSTER threads_per_unit must be M, 2M, ... <= 32"); return LJSEL_ERR_UNSUPPORTED; }
-        if (c->newton3 && t != M) { set_error("CLUSTER with N3L uses threads_per_unit = M"); return LJSEL_ERR_UNSUPPORTED; }
     } else if (c->method == LJSEL_METHOD_VLW) {
         if (t != 1) { set_error("VLW uses threads_per_unit = 1"); return LJSEL_ERR_UNSUPPORTED; }
         if (c->csf != 1.0) { set_error("VLW uses csf = 1"); return LJSEL_ERR_UNSUPPORTED; }
@@ -124,8 +123,8 @@ ljsel_status validate_config(const System &s, const ljsel_config *c) {
         if (t != 1) { set_error("LC uses threads_per_unit = 1"); return LJSEL_ERR_UNSUPPORTED; }
     }
     const bool walled = s.params.walls[0] || s.params.walls[1] || s.params.walls[2];
-    if (walled && (c->method == LJSEL_METHOD_VLW || c->method == LJSEL_METHOD_CLUSTER)) {
-        set_error("reflective walls are available with the LC and VL methods");
+    if (walled && c->method == LJSEL_METHOD_VLW) {
+        set_error("reflective walls are available with the LC, VL and CLUSTER methods");
         return LJSEL_ERR_UNSUPPORTED;
     }
     if (s.params.skin == 0.0 && c->method != LJSEL_METHOD_LC && c->rebuild_interval != 1) {
@@ -151,7 +150,7 @@ std::vector<Buf *> System::all_bufs() {
     return {&b_x[0], &b_x[1], &b_v[0], &b_v[1], &b_id[0], &b_id[1], &b_type[0], &b_type[1], &b_pos[0], &b_pos[1],
             &b_xref, &b_force, &b_cell_count, &b_cell_start, &b_clcell_start, &b_cell_of, &b_slot_of, &b_key_of,
             &b_tmp_idx, &b_tmp_key, &b_cell_sorted, &b_scan, &b_nl, &b_nl_count, &b_strips, &b_nstrips, &b_cl_first, &b_cl_count,
-            &b_cl_cell, &b_cl_lo, &b_cl_hi, &b_cp, &b_cp_count, &b_ncl, &b_ctrl, &b_io,
+            &b_cl_cell, &b_cp, &b_cp_count, &b_ncl, &b_ctrl, &b_io,
             &b_adj_cot, &b_adj_x, &b_adj_v, &b_adj_theta, &b_ckpt, &b_seg, &b_stats};
 }
 
@@ -271,22 +270,22 @@ ljsel_status System::apply_config() {
     if (cfg.method == LJSEL_METHOD_CLUSTER) {
         ncl_cap = n / M + ncell + 1;
         if (cp_cap <= 0) {
-            // clusters per stencil at the mean occupancy, with room
-            const double occ = (double)n / ncell;
-            const double per_cell = std::max(1.0, std::ceil(occ / M));
-            const int stencil = (2 * reach + 1) * (2 * reach + 1) * (2 * reach + 1);
-            double est = 1.3 * stencil * per_cell + 8;
+            // the union of M members' neighbourhoods: a sphere of the list
+            // radius widened by about the cluster's radius, with room
+            const double vol = params.box[0] * params.box[1] * params.box[2];
+            const double rho = n / vol;
+            const double grow_r = 0.62 * std::cbrt(M / std::max(rho, 1e-12));
+            const double rr = std::min(rlist + grow_r, 2.0 * rlist);
+            double est = 4.18879 * rr * rr * rr * rho * 1.3 + 16;
             if (cfg.newton3) est = est * 0.5 + 8;
-            cp_cap = (int)std::min(est, 8192.0);
+            cp_cap = (int)std::min(est, 16384.0);
         }
-        cp_stride = ((ncl_cap + 31) / 32) * 32;
+        cp_cap = (cp_cap + 3) & ~3;
         LJ_TRY(grow(b_cl_first, (size_t)ncl_cap * 4));
         LJ_TRY(grow(b_cl_count, (size_t)ncl_cap * 4));
         LJ_TRY(grow(b_cl_cell, (size_t)ncl_cap * 4));
-        LJ_TRY(grow(b_cl_lo, (size_t)ncl_cap * p4()));
-        LJ_TRY(grow(b_cl_hi, (size_t)ncl_cap * p4()));
-        LJ_TRY(grow(b_cp, (size_t)cp_cap * cp_stride * 4));
-        LJ_TRY(grow(b_cp_count, (size_t)cp_stride * 4));
+        LJ_TRY(grow(b_cp, (size_t)cp_cap * ncl_cap * 4));
+        LJ_TRY(grow(b_cp_count, (size_t)ncl_cap * 4));
     }
     (void)grew;
     gexec = nullptr;  // the next advance looks the configuration up in the graph cache
@@ -344,12 +343,9 @@ template <typename R> void System::fill_dev(Dev<R> &S) const {
     S.cl_first = (int *)b_cl_first.ptr;
     S.cl_count = (int *)b_cl_count.ptr;
     S.cl_cell = (int *)b_cl_cell.ptr;
-    S.cl_lo = (V4<R> *)b_cl_lo.ptr;
-    S.cl_hi = (V4<R> *)b_cl_hi.ptr;
     S.cp = (uint32_t *)b_cp.ptr;
     S.cp_count = (int *)b_cp_count.ptr;
     S.cp_cap = cp_cap;
-    S.cp_stride = cp_stride;
     S.ncl_total = (int *)b_ncl.ptr;
     S.ctrl = (Ctrl *)b_ctrl.ptr;
     const int nt = params.ntypes;

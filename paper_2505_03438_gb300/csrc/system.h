@@ -63,7 +63,7 @@ struct System {
     int M = 1;
     // list capacities
     int nl_cap = 0;
-    int ncl_cap = 0, cp_cap = 0, cp_stride = 0;
+    int ncl_cap = 0, cp_cap = 0;
     long long capacity_retries = 0;
     bool cap_fitted = false;  // the Verlet-list row capacity was fitted to a build
     bool structure_dirty = true;
@@ -74,7 +74,7 @@ struct System {
     Buf b_cell_count, b_cell_start, b_clcell_start, b_cell_of, b_slot_of, b_key_of, b_tmp_idx, b_tmp_key,
         b_cell_sorted, b_scan;
     Buf b_nl, b_nl_count, b_strips, b_nstrips;
-    Buf b_cl_first, b_cl_count, b_cl_cell, b_cl_lo, b_cl_hi, b_cp, b_cp_count, b_ncl;
+    Buf b_cl_first, b_cl_count, b_cl_cell, b_cp, b_cp_count, b_ncl;
     Buf b_ctrl, b_io;
     // gradients: sorted cotangent, caller-order adjoint state, parameter
     // sums, rollout checkpoints and the recomputed segment

@@ -51,14 +51,17 @@ CONFIGS = [
     dict(method="VL", newton3=True, threads_per_unit=1, csf=0.5),
     dict(method="VLW", newton3=False),
     dict(method="VLW", newton3=True),
+    dict(method="CL", cluster_size=2, newton3=False, threads_per_unit=2),
+    dict(method="CL", cluster_size=2, newton3=False, threads_per_unit=8),
+    dict(method="CL", cluster_size=2, newton3=True, threads_per_unit=4),
     dict(method="CL", cluster_size=4, newton3=False, threads_per_unit=4),
     dict(method="CL", cluster_size=4, newton3=False, threads_per_unit=16),
-    dict(method="CL", cluster_size=4, newton3=True, threads_per_unit=4),
+    dict(method="CL", cluster_size=4, newton3=True, threads_per_unit=8),
     dict(method="CL", cluster_size=8, newton3=False, threads_per_unit=8),
     dict(method="CL", cluster_size=8, newton3=False, threads_per_unit=32),
     dict(method="CL", cluster_size=8, newton3=True, threads_per_unit=8),
-    dict(method="CL", cluster_size=32, newton3=False, threads_per_unit=32),
-    dict(method="CL", cluster_size=32, newton3=True, threads_per_unit=32),
+    dict(method="CL", cluster_size=4, newton3=False, threads_per_unit=8, csf=0.5),
+    dict(method="CL", cluster_size=4, newton3=True, threads_per_unit=4, csf=0.5),
 ]
 
 
@@ -365,7 +368,9 @@ def test_liquid_1m_full_size(lj):
 
 SMALL_BOX_CFGS = [dict(method="VL"), dict(method="VL", newton3=True), dict(method="VL", csf=0.5),
                   dict(method="VL", newton3=True, csf=0.5), dict(method="LC"), dict(method="LC", csf=0.5),
-                  dict(method="CL", cluster_size=4, threads_per_unit=4), dict(method="VLW")]
+                  dict(method="CL", cluster_size=4, threads_per_unit=4),
+                  dict(method="CL", cluster_size=2, newton3=True, threads_per_unit=2),
+                  dict(method="CL", cluster_size=8, newton3=True, threads_per_unit=8, csf=0.5), dict(method="VLW")]
 
 
 @pytest.mark.parametrize("cfg", SMALL_BOX_CFGS, ids=lambda c: "-".join("%s%s" % kv for kv in c.items()))

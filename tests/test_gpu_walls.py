@@ -3,7 +3,8 @@ the FP64 oracle (the walled heating-sphere conditions of Sec. 6).
 
 Between walls a dimension has no periodic image, and a particle that
 crosses a wall after a drift is mirrored back with its velocity component
-reversed.  Walls are available with the linked-cell and Verlet-list methods.
+reversed.  Walls are available with the linked-cell, Verlet-list and
+cluster-list methods.
 """
 import numpy as np
 import pytest
@@ -16,7 +17,10 @@ pytestmark = pytest.mark.gpu
 
 CONFIGS = [dict(method="LC"), dict(method="LC", newton3=True), dict(method="LC", csf=0.5),
            dict(method="VL"), dict(method="VL", threads_per_unit=4), dict(method="VL", newton3=True),
-           dict(method="VL", csf=0.5), dict(method="VL", newton3=True, csf=0.5)]
+           dict(method="VL", csf=0.5), dict(method="VL", newton3=True, csf=0.5),
+           dict(method="CL", cluster_size=4, threads_per_unit=8), dict(method="CL", cluster_size=2, threads_per_unit=2),
+           dict(method="CL", cluster_size=8, newton3=True, threads_per_unit=8),
+           dict(method="CL", cluster_size=4, newton3=True, threads_per_unit=4, csf=0.5)]
 
 
 def _gas(seed, L=11.0, n=500):
@@ -53,7 +57,7 @@ def test_pairs_and_forces_with_walls(walls, cfg):
         assert abs(e - ref["U"]) < max(tol, 2e-6) * abs(ref["U"])
 
 
-@pytest.mark.parametrize("method", ["LC", "VL"])
+@pytest.mark.parametrize("method", ["LC", "VL", "CL"])
 def test_walled_liquid_trajectory_fp64(method):
     x, box = scenarios.fcc_lattice(4, 0.7)
     L = box[0] + 1.0
@@ -61,7 +65,7 @@ def test_walled_liquid_trajectory_fp64(method):
     rng = np.random.default_rng(41)
     v = scenarios.maxwell_boltzmann(len(x), 1.5, 1.0, rng)
     s = lj.System(x=x, v=v, box=np.full(3, L), walls=(1, 1, 1), precision=1, dt=0.002)
-    s.set_config(method=method, rebuild_interval=10)
+    s.set_config(method=method, rebuild_interval=10, **(dict(cluster_size=4, threads_per_unit=8) if method == "CL" else {}))
     s.step(300)
     xg, vg = s.state()
     p = oracle.make_params(L, 1.0, 1.0, 2.5, True, walls=(1, 1, 1))
@@ -122,12 +126,11 @@ def test_heating_in_walls_follows_the_oracle_fp64():
     assert temps[-1] > temps[0]
 
 
-def test_walls_with_window_or_cluster_lists_are_refused():
+def test_walls_with_window_lists_are_refused():
     sc = scenarios.random_gas(500, 11.0, seed=35, min_dist=0.85)
     s = lj.System(sc, walls=(1, 1, 1))
-    for cfg in (dict(method="VLW"), dict(method="CL", cluster_size=8, threads_per_unit=8)):
-        with pytest.raises(lj.LjselError) as e:
-            s.set_config(**cfg)
-        assert e.value.status == 9
+    with pytest.raises(lj.LjselError) as e:
+        s.set_config(method="VLW")
+    assert e.value.status == 9
     chosen, rep = s.autotune(strategy="full", trial_steps=2)
-    assert chosen.method in (lj.METHOD_LC, lj.METHOD_VL)
+    assert chosen.method in (lj.METHOD_LC, lj.METHOD_VL, lj.METHOD_CLUSTER)
