@@ -378,16 +378,16 @@ __device__ __forceinline__ float &half_of(float2 &v, int b) { return b ? v.y : v
 __device__ __forceinline__ float half_of(const float2 &v, int b) { return b ? v.y : v.x; }
 
 struct FastTab {
-    float2 sig2, e48, ne24;
-    float2 nmid;   // -(lo + hi) / 2: r^2 + nmid is the distance from the band's centre
-    float lo, hi;  // FP32 band around r_c^2 (as in Cut<float>)
-    float halfw;   // (hi - lo) / 2 with a small margin: |r^2 + nmid| <= halfw covers the band
+    float2 a2, nb2;     // 48 eps sigma^12 and -24 eps sigma^6: f/r = s^4 (a s^3 - b) with s = 1 / r^2
+    float lo, hi;       // FP32 band around r_c^2 (as in Cut<float>)
+    unsigned lo_bits;   // bit pattern of lo; r^2 >= 0 orders like its bit pattern
+    unsigned band_bits; // bits(hi) - bits(lo): lo <= r^2 <= hi iff bits(r^2) - bits(lo) <= band_bits (unsigned)
 };
 
 // One listed particle j against the members: returns whether r^2 of some
-// pair came within halfw of the band's centre (a superset of the band).
-// With EXCL the entry is the cluster's own member b (see cl_entry): member
-// m's half counts only when m != b (without N3L) or m < b (with N3L).
+// counted pair fell in the band (those pairs are left out here).  With EXCL
+// the entry is the cluster's own member b (see cl_entry): member m's half
+// counts only when m != b (without N3L) or m < b (with N3L).
 template <int M, bool N3L, bool EXCL = false>
 __device__ __forceinline__ bool fast_entry(const float4 &pj, const float2 (&mx)[M / 2], const float2 (&my)[M / 2],
                                            const float2 (&mz)[M / 2], float2 (&fx)[M / 2], float2 (&fy)[M / 2],
@@ -401,19 +401,14 @@ __device__ __forceinline__ bool fast_entry(const float4 &pj, const float2 (&mx)[
         float2 r2 = __fmul2_rn(dx, dx);
         r2 = __ffma2_rn(dy, dy, r2);
         r2 = __ffma2_rn(dz, dz, r2);
-        const float2 dc = __fadd2_rn(r2, t.nmid);
-        near = near || fabsf(dc.x) <= t.halfw || fabsf(dc.y) <= t.halfw;
         const bool ka = !EXCL || (N3L ? 2 * h < b : 2 * h != b);
         const bool kb = !EXCL || (N3L ? 2 * h + 1 < b : 2 * h + 1 != b);
-        const float2 in = make_float2(ka && r2.x < t.lo ? 1.f : 0.f, kb && r2.y < t.lo ? 1.f : 0.f);
-
-        // an excluded half (the member itself, at distance 0) gets 1/r^2 = 0,
-        // so that no infinity meets the zero mask
-        const float2 ri = EXCL ? make_float2(ka ? fast_rcp(r2.x) : 0.f, kb ? fast_rcp(r2.y) : 0.f)
-                               : make_float2(fast_rcp(r2.x), fast_rcp(r2.y));
-        const float2 sr2 = __fmul2_rn(t.sig2, ri);
-        const float2 sr6 = __fmul2_rn(__fmul2_rn(sr2, sr2), sr2);
-        const float2 fr = __fmul2_rn(__fmul2_rn(__fmul2_rn(sr6, ri), __ffma2_rn(t.e48, sr6, t.ne24)), in);
+        near = near || (ka && __float_as_uint(r2.x) - t.lo_bits <= t.band_bits) ||
+               (kb && __float_as_uint(r2.y) - t.lo_bits <= t.band_bits);
+        // out of range or excluded (the member itself, at distance 0): s = 0
+        const float2 sv = make_float2(ka && r2.x < t.lo ? fast_rcp(r2.x) : 0.f, kb && r2.y < t.lo ? fast_rcp(r2.y) : 0.f);
+        const float2 s2 = __fmul2_rn(sv, sv);
+        const float2 fr = __fmul2_rn(__fmul2_rn(s2, s2), __ffma2_rn(t.a2, __fmul2_rn(s2, sv), t.nb2));
         fx[h] = __ffma2_rn(fr, dx, fx[h]);
         fy[h] = __ffma2_rn(fr, dy, fy[h]);
         fz[h] = __ffma2_rn(fr, dz, fz[h]);
@@ -487,13 +482,12 @@ __global__ void __launch_bounds__(CL_THREADS, M == 2 ? 6 : (M == 4 ? 5 : 4)) k_c
         fx[h] = fy[h] = fz[h] = f2(0.f);
     }
     FastTab t;
-    t.sig2 = f2(S.tab.sig2[0]);
-    t.e48 = f2(S.tab.e48[0]);
-    t.ne24 = f2(-S.tab.e24[0]);
+    t.a2 = f2(S.tab.a12[0]);
+    t.nb2 = f2(-S.tab.b6[0]);
     t.lo = S.tab.rc2lo[0];
     t.hi = S.tab.rc2hi[0];
-    t.nmid = f2(-0.5f * (t.lo + t.hi));
-    t.halfw = 0.5f * (t.hi - t.lo) * 1.0625f;
+    t.lo_bits = __float_as_uint(t.lo);
+    t.band_bits = __float_as_uint(t.hi) - t.lo_bits;
     const int cap = S.cp_cap;
     const uint32_t *row = S.cp + (size_t)(cvalid ? c : 0) * cap;
     const int nq = (nf + 3) >> 2;

@@ -80,6 +80,7 @@ template <typename R> struct PairTab {
     R rc2lo[MAXT2], rc2hi[MAXT2];
     double rc2d[MAXT2];
     R inv_sig[MAXT2];      // 1 / sigma (parameter derivatives)
+    R a12[MAXT2], b6[MAXT2];  // 48 eps sigma^12, 24 eps sigma^6: f/r = s^4 (a12 s^3 - b6), s = 1 / r^2
     R inv_mass_dt[MAXT];   // dt / m per type
     double dt;
     double half_mass[MAXT];

@@ -364,6 +364,9 @@ template <typename R> void System::fill_dev(Dev<R> &S) const {
             S.tab.e24[t] = (R)(24.0 * e);
             S.tab.e48[t] = (R)(48.0 * e);
             S.tab.e4[t] = (R)(4.0 * e);
+            const double sg6 = sg * sg * sg * sg * sg * sg;
+            S.tab.a12[t] = (R)(48.0 * e * sg6 * sg6);
+            S.tab.b6[t] = (R)(24.0 * e * sg6);
             S.tab.ushift[t] = params.shift_potential ? (R)uc : (R)0;
             S.tab.rc2d[t] = rc * rc;
             S.tab.rc2lo[t] = (R)(rc * rc * (1.0 - 1.0 / 16384.0));
