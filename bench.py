@@ -1,19 +1,25 @@
 #!/usr/bin/env python
 """Benchmark: LJ particle-steps/s on the homogeneous 1M-atom liquid, the
 auto-tuned GPU path against every fixed configuration, with the roofline
-fraction of the dominant kernel.
+fraction of the dominant kernel and of the whole step.
 
 Workload (synthetic; the paper's md-flexible inputs are not available):
 N = 1,048,576 LJ particles on a 64^3 x 4 fcc lattice, density 0.8442,
 Maxwell-Boltzmann velocities at T = 0.72 (seed 2), cutoff 2.5 sigma with an
 energy shift, skin 0.3 sigma, rebuild every 10 steps (or earlier when a
-particle moves skin/2), dt 0.005, 1000 steps per run, FP32 pair arithmetic
-with FP64 integration and sums.
+particle moves skin/2), dt 0.005, FP32 pair arithmetic with FP64
+integration and sums.
 
 A "step" is one Stormer-Verlet step of the whole system (binning, lists,
-forces, update).  The timed region of the default run holds one Full Search
-tuning phase (its trial steps advance the simulation and count as steps)
-followed by the remaining steps with the chosen configuration.
+forces, update).  The timed region of the headline run holds one tuning
+phase (with the default Random Forest strategy: the live statistics, the
+forest's choice and the switch to it; trial steps of other strategies
+advance the simulation and count as steps) followed by the remaining steps
+with the chosen configuration.
+
+Output: one compact JSON line (the last line printed); the per-leg details
+(every fixed configuration, the other strategies, the batched, gradient and
+heated-sphere legs) go to the file given by --details.
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
 
@@ -36,18 +42,29 @@ sys.path.insert(0, ROOT)
 
 METRIC = "LJ particle-steps/s at 1M atoms, auto-tuned vs fixed config; % of roofline"
 UNIT = "particle-steps/s"
+WORKLOAD = "lj_liquid_1m: N=1048576 fcc 64^3x4, rho 0.8442, T 0.72, rc 2.5, skin 0.3, R 10"
 # Algorithmic FP32 work per within-cutoff unordered pair with Newton's third
 # law (FFMA = 2 flops): displacement 3, r^2 5, cutoff test 1, (sigma/r)^6 3,
-# f/r 4, F_i 6, F_j 6.  The reciprocal runs on the MUFU pipe and is not counted.
+# f/r 4, F_i 6, F_j 6.  The reciprocal runs on the MUFU pipe and is counted
+# against its own peak.
 FLOPS_PER_PAIR = 28
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
-# DRAM bytes (read + write) of one launch of the Verlet-list force kernel
-# fused with the update (N3L off, two lanes per particle, fitted row
-# capacity), N = 1,048,576, from the ncu capture summarised in
-# profiles/liquid_1m_force_vl_ncu.md.  Valid only for that kernel at that
-# size; reported as null for any other chosen configuration.
-VL_STEP_TRAFFIC_1M = 491804928 + 58008832
+# Algorithmic per-particle figures of the other kernels of a step:
+# the Stormer-Verlet update reads and writes the FP64 x, v (96 B), writes the
+# FP32 working position (16 B) and reads the force (16 B), and issues about
+# 12 FP64 instructions (3 conversions and 3 adds for v, 3 fused multiply-adds
+# for x, 3 conversions to FP32); a rebuild reads the working position and
+# writes the sorted one and the permutation (36 B), 8 B per cell, reads the
+# position once more for the lists (16 B) and writes 4 B per list entry.
+UPDATE_BYTES_PER_PARTICLE = 128
+UPDATE_FP64_PER_PARTICLE = 12
+REBUILD_BYTES_PER_PARTICLE = 36 + 16
+REBUILD_BYTES_PER_CELL = 8
+LIST_BYTES_PER_ENTRY = 4
+# DRAM bytes (read + write) of one launch of the Verlet-list force kernel fused
+# with the update (N3L off, two lanes per particle), N = 1,048,576, from an
+# ncu capture of that kernel; reported only when that configuration is the
+# chosen one.
+VL_T2_TRAFFIC_1M = {"config": "VL-noN3L-t2", "bytes": 491804928 + 58008832}
 
 
 def max_over_ranks(ms, dist=None, device="cpu"):
@@ -74,9 +91,11 @@ def measured_peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    """nvidia-smi sampling of SM clocks and throttle reasons, started before
+    the warm-up and stopped after the timed region (the timed region alone is
+    often shorter than the sampling interval)."""
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, interval_ms=10):
         self.path = tempfile.mktemp(suffix=".csv")
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -84,14 +103,16 @@ class Clocks:
         try:
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + q,
-                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                       "--format=csv,noheader,nounits", "-lms", str(interval_ms)], stdout=self.f,
                                       stderr=subprocess.DEVNULL)
+            time.sleep(0.3)  # the first sample takes a moment
         except Exception:
             self.p = None
 
     def stop(self):
         if self.p is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.05)
         self.p.terminate()
         try:
             self.p.wait(timeout=5)
@@ -114,7 +135,24 @@ class Clocks:
                     reasons.add(nm)
         os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "window": "warm-up and timed region"}
+
+
+def step_roofline(n, npairs, n3l, entries, ncell, rebuild_every, peaks, hbm_gbs):
+    """Per-step roofline time T_roof = sum over the kernels of
+    max(bytes / HBM bandwidth, operations / pipe peak), the rebuild amortised
+    over the measured interval: the force kernel against the FP32 and MUFU
+    peaks (algorithmic pairs only, N3L work), the update against HBM and
+    FP64, the rebuild against HBM."""
+    fp32 = max(peaks["fp32_tflops"], peaks["fp32x2_tflops"]) * 1e12
+    t_force = max(npairs * FLOPS_PER_PAIR / fp32, npairs / (peaks["rcp_tops"] * 1e12))
+    t_update = max(n * UPDATE_BYTES_PER_PARTICLE / (hbm_gbs * 1e9),
+                   n * UPDATE_FP64_PER_PARTICLE / (peaks["fp64_tflops"] * 1e12 / 2.0))
+    reb_bytes = n * REBUILD_BYTES_PER_PARTICLE + ncell * REBUILD_BYTES_PER_CELL + entries * LIST_BYTES_PER_ENTRY
+    t_rebuild = reb_bytes / (hbm_gbs * 1e9)
+    t = t_force + t_update + t_rebuild / max(rebuild_every, 1.0)
+    return {"t_roof_us": 1e6 * t, "force_us": 1e6 * t_force, "update_us": 1e6 * t_update,
+            "rebuild_us": 1e6 * t_rebuild, "rebuild_every": rebuild_every}
 
 
 def oracle_rate(sc, budget_s=12.0):
@@ -125,16 +163,17 @@ def oracle_rate(sc, budget_s=12.0):
     p = oracle.make_params(sc["box"], sc["eps"], sc["sigma"], sc["rcut"], True)
     cell_min = 2.5 + sc["skin"]
     t0 = time.perf_counter()
-    oracle.verlet_run(sc["x"], sc["v"], sc["types"], sc["mass"], p, sc["dt"], 1, cell_min=cell_min, nthreads=cores)
+    oracle.verlet_run(sc["x"], sc["v"], sc.get("types"), sc["mass"], p, sc["dt"], 1, cell_min=cell_min, nthreads=cores)
     t1 = time.perf_counter()
     per = (t1 - t0) / 2.0  # one call evaluates forces twice for one step
     nsteps = max(1, min(50, int(budget_s / max(per, 1e-3))))
     t0 = time.perf_counter()
-    oracle.verlet_run(sc["x"], sc["v"], sc["types"], sc["mass"], p, sc["dt"], nsteps, cell_min=cell_min,
+    oracle.verlet_run(sc["x"], sc["v"], sc.get("types"), sc["mass"], p, sc["dt"], nsteps, cell_min=cell_min,
                       nthreads=cores)
     t1 = time.perf_counter()
     n = len(sc["x"])
-    return {"value": n * nsteps / (t1 - t0), "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": n * nsteps / (t1 - t0), "unit": UNIT, "cores": cores, "kind": "oracle", "steps": nsteps,
+            "seconds": t1 - t0,
             "sample": "%d Stormer-Verlet steps of the N=%d liquid (FP64 linked cells, %d OpenMP threads)" %
                       (nsteps, n, cores)}
 
@@ -183,7 +222,7 @@ def adjoint_leg(reps=20, nsteps=50, every=10):
     return out
 
 
-def batch_leg(steps=500, warmup=5, trial_steps=10, profile_steps=30, eager=False):
+def batch_leg(peaks, steps=500, warmup=5, trial_steps=10, profile_steps=30, eager=False):
     """Batched replicas (512 periodic systems, N log-uniform in [256, 8192],
     about 1.17M particles): tile chosen by the batch autotuner, then `steps`
     steps in one graph launch timed with CUDA events on the batch's stream."""
@@ -210,9 +249,7 @@ def batch_leg(steps=500, warmup=5, trial_steps=10, profile_steps=30, eager=False
     c1 = b.counters()
     prof = b.profile(profile_steps)
     npairs = len(b.pairs())
-    peaks = measured_peaks()
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    fp32_peak = max(peaks["fp32_tflops"], peaks["fp32x2_tflops"])
     ach = npairs * FLOPS_PER_PAIR / (prof["force_ms"] * 1e-3) / 1e12 if prof["force_ms"] > 0 else None
     out = {"workload": "replicas_512: N log-uniform [256, 8192] (sum %d), rho U[0.3, 0.9], T U[0.7, 2.0], "
                        "rc 2.5, skin 0.3, R 10" % b.ntot,
@@ -225,7 +262,8 @@ def batch_leg(steps=500, warmup=5, trial_steps=10, profile_steps=30, eager=False
            "kernel_ms": {k: prof[k] for k in ("rebuild_ms", "force_ms", "control_ms")},
            "roofline": {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
                         "frac": ach / fp32_peak if ach else None, "traffic": None,
-                        "kernel": "batched force + update", "flops_per_launch": npairs * FLOPS_PER_PAIR}}
+                        "kernel": "batched force + update", "flops_per_launch": npairs * FLOPS_PER_PAIR,
+                        "peak_basis": "measured FP32 probe (ljsel_measure_peaks)"}}
     b.close()
     return out
 
@@ -319,7 +357,9 @@ def inhomogeneous_leg(steps=20000, every=1000, strategy="predictive", fixed_step
 
 
 def run_reference(args):
-    """Reference arm: the oracle as it stands, on the host cores."""
+    """Reference arm: the oracle as it stands, on the host cores.  Every
+    --steps step is a bounded sample (the budget scales with the requested
+    steps); the line reports the steps actually timed."""
     from paper_2505_03438_gb300 import scenarios
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -327,9 +367,9 @@ def run_reference(args):
     sc = scenarios.liquid_1m()
     cb = oracle_rate(sc, budget_s=min(60.0, 6.0 + 2.0 * args.steps / 100.0))
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * len(sc["x"]) / cb["value"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "lj_liquid_1m: N=1048576 fcc 64^3x4, rho 0.8442, T 0.72, rc 2.5, skin 0.3"},
+            "steps": cb["steps"], "steps_requested": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * cb["seconds"] / cb["steps"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD},
             "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -361,6 +401,12 @@ def run_ours(args):
     v = torch.tensor(sc["v"], device="cuda")
     t = torch.zeros(n, dtype=torch.int32, device="cuda")
     params = lj.make_params(sc["box"], skin=sc["skin"], dt=sc["dt"], use_graphs=not args.eager)
+    peaks = lj.ljsel_measure_peaks(30.0)  # FP32, FP32x2, FP64 and reciprocal rates of this GPU
+    hbm = measured_peaks().get("hbm_gbs", 6800.0)
+    model = lj_forest.load()
+    fixed_cfg = (lj.make_config(args.method, cluster_size=args.cluster, newton3=args.newton3,
+                                threads_per_unit=args.tpu, rebuild_interval=sc["rebuild"], csf=args.csf)
+                 if args.method else None)
 
     def barrier():
         if dist is not None:
@@ -368,10 +414,8 @@ def run_ours(args):
 
     def fresh():
         hh = lj.ljsel_create(params, n, x, v, t, stream.cuda_stream)
-        if args.method:
-            lj.ljsel_set_config(hh, lj.make_config(args.method, cluster_size=args.cluster, newton3=args.newton3,
-                                                   threads_per_unit=args.tpu, rebuild_interval=sc["rebuild"],
-                                                   csf=args.csf))
+        if fixed_cfg is not None:
+            lj.ljsel_set_config(hh, fixed_cfg)
         lj.ljsel_step(hh, W)  # warm-up
         torch.cuda.synchronize()
         return hh
@@ -381,7 +425,7 @@ def run_ours(args):
         the K steps, bracketed by a barrier and device synchronisation.  The
         Random Forest strategy's forest is installed before it."""
         if strategy == "forest":
-            lj.ljsel_set_forest(hh, lj_forest.load())
+            lj.ljsel_set_forest(hh, model)
         c0 = lj.ljsel_get_counters(hh)
         barrier()
         torch.cuda.synchronize()
@@ -401,13 +445,11 @@ def run_ours(args):
         barrier()
         ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
         c1 = lj.ljsel_get_counters(hh)
-        steps = c1["steps"] - c0["steps"]
-        return {"ms": ms, "steps": steps, "chosen": chosen, "rep": rep,
+        return {"ms": ms, "steps": c1["steps"] - c0["steps"], "chosen": chosen, "rep": rep,
                 "rebuilds": c1["rebuilds"] - c0["rebuilds"], "early": c1["early_rebuilds"] - c0["early_rebuilds"]}
 
     headline = args.strategy if args.tune else None
-    other = [st for st in ("expert", "full", "forest") if args.tune and args.other and st != headline]
-    # the other strategy first, so the headline run is the last before profiling
+    other = [st for st in ("expert", "full", "predictive", "forest") if args.tune and args.other and st != headline]
     extra_runs = {}
     for st in other:
         hx = fresh()
@@ -415,31 +457,37 @@ def run_ours(args):
         extra_runs[st] = {"value": job_throughput(world, n, r["steps"], r["ms"]), "chosen": r["chosen"].name(),
                           "tuner": r["rep"]}
         lj.ljsel_destroy(hx)
-    h = fresh()
     clk = Clocks(local)
+    h = fresh()
     run = timed(h, headline)
     clocks = clk.stop()
     ms, steps_done, chosen, rep = run["ms"], run["steps"], run["chosen"], run["rep"]
     value = job_throughput(world, n, steps_done, ms)
     chosen_name = chosen.name()
+    # further tuned runs, for a median against the best fixed configuration
+    tuned_values = [value]
+    for _ in range(max(0, args.repeats - 1)):
+        hx = fresh()
+        r = timed(hx, headline)
+        tuned_values.append(job_throughput(world, n, r["steps"], r["ms"]))
+        lj.ljsel_destroy(hx)
 
     # ---- per-kernel timing (CUDA events around each launch) ---------------
     prof = lj.ljsel_profile_steps(h, args.profile_steps)
     _, npairs = lj.ljsel_get_pairs(h, 0)
     cnt = lj.ljsel_get_counters(h)
 
-    # ---- every fixed configuration, same workload: from the same initial
-    # state, the same warm-up, the same K timed steps ----------------------
-    fixed = {}
+    # ---- every fixed configuration from the same initial state, the same
+    # warm-up and the same K timed steps; the best three again, repeatedly
+    fixed, fixed_eff, best = {}, {}, None
     if args.fixed_steps != 0:
         kf = K if args.fixed_steps < 0 else args.fixed_steps
-        for c in lj.ljsel_default_candidates(h):
+        cands = {c.name(): c for c in lj.ljsel_default_candidates(h)}
+
+        def run_fixed(c):
             lj.ljsel_set_state(h, x, v)
             lj.ljsel_set_config(h, c)
-            try:
-                lj.ljsel_step(h, W)
-            except lj.LjselError:
-                continue  # not available for this system
+            lj.ljsel_step(h, W)
             torch.cuda.synchronize()
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
@@ -447,106 +495,150 @@ def run_ours(args):
             lj.ljsel_step(h, kf)
             b.record(stream)
             torch.cuda.synchronize()
-            fixed[c.name()] = n * kf / (a.elapsed_time(b) * 1e-3)
+            return n * kf / (a.elapsed_time(b) * 1e-3)
+
+        for name, c in cands.items():
+            try:
+                fixed[name] = run_fixed(c)
+            except lj.LjselError:
+                continue  # not available for this system
+            ct = lj.ljsel_get_counters(h)
+            _, np_c = lj.ljsel_get_pairs(h, 0)
+            slots = ct["list_entries"] * (c.cluster_size if c.method == lj.METHOD_CLUSTER else 1)
+            fixed_eff[name] = (np_c * (1 if c.newton3 else 2) / slots) if slots else None
+        top = sorted(fixed, key=lambda k: -fixed[k])[:3]
+        remeasured = {k: statistics.median([run_fixed(cands[k]) for _ in range(max(1, args.repeats))]) for k in top}
+        bname = max(remeasured, key=remeasured.get)
+        best = {"name": bname, "value": remeasured[bname], "steps": kf, "remeasured_top3": remeasured}
     lj.ljsel_destroy(h)
 
-    # ---- end to end through the C ABI with host buffers -------------------
+    # ---- end to end through the C ABI with pinned host buffers ------------
     e2e = None
     if args.e2e:
-        xh = np.ascontiguousarray(sc["x"])
-        vh = np.ascontiguousarray(sc["v"])
-        th = np.zeros(n, np.int32)
-        xo = np.empty_like(xh)
-        vo = np.empty_like(vh)
-        model = lj_forest.load() if args.tune and args.strategy == "forest" else None
+        xp = torch.from_numpy(np.ascontiguousarray(sc["x"])).pin_memory()
+        vp = torch.from_numpy(np.ascontiguousarray(sc["v"])).pin_memory()
+        tp = torch.zeros(n, dtype=torch.int32).pin_memory()
+        xo = torch.empty_like(xp).pin_memory()
+        vo = torch.empty_like(vp).pin_memory()
+        xh, vh, th, xoh, voh = xp.numpy(), vp.numpy(), tp.numpy(), xo.numpy(), vo.numpy()
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
         hp = lj.make_params(sc["box"], skin=sc["skin"], dt=sc["dt"], use_graphs=not args.eager)
         h2 = lj.ljsel_create(hp, n, xh, vh, th, stream.cuda_stream)
         done2 = 0
-        if model is not None:
-            lj.ljsel_set_forest(h2, model)
         if args.tune:
+            if args.strategy == "forest":
+                lj.ljsel_set_forest(h2, model)
             _, r2 = lj.ljsel_autotune(h2, strategy=args.strategy, trial_steps=args.trial_steps,
                                       probe_steps=args.probe_steps, probe_factor=2.0)
             done2 = r2["trial_steps_total"]
         lj.ljsel_step(h2, max(0, K - done2))
-        lj.ljsel_get_state(h2, xo, vo)
+        lj.ljsel_get_state(h2, xoh, voh)
         t1 = time.perf_counter()
         lj.ljsel_destroy(h2)
         barrier()
-        e2e = {"value": world * n * K / (t1 - t0), "unit": UNIT,
+        e2e = {"value": world * n * K / (t1 - t0), "unit": UNIT, "host_buffers": "pinned",
                "h2d_bytes_per_step": (xh.nbytes + vh.nbytes + th.nbytes) / K,
-               "d2h_bytes_per_step": (xo.nbytes + vo.nbytes) / K}
+               "d2h_bytes_per_step": (xoh.nbytes + voh.nbytes) / K}
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
+    emit(args, locals())
+    if dist is not None:
+        dist.destroy_process_group()
 
-    peaks = measured_peaks()
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+
+def emit(args, L):
+    """Rank 0: the compact headline line (printed last) and the details file."""
+    import paper_2505_03438_gb300 as lj
+    sc, n, K, W, prof, peaks, chosen, rep, run = (L[k] for k in ("sc", "n", "K", "W", "prof", "peaks", "chosen",
+                                                                  "rep", "run"))
+    npairs, cnt, hbm, world = L["npairs"], L["cnt"], L["hbm"], L["world"]
+    ms, steps_done, value = L["ms"], L["steps_done"], L["value"]
+    chosen_name = chosen.name()
+    # ---- roofline of the dominant kernel (force, fused with the update when
+    # N3L is off), against the measured FP32 peak of this GPU -----------------
+    fp32_peak = max(peaks["fp32_tflops"], peaks["fp32x2_tflops"])
     force_ms = prof["force_ms"]
     achieved = npairs * FLOPS_PER_PAIR / (force_ms * 1e-3) / 1e12 if force_ms > 0 else None
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    traffic = VL_STEP_TRAFFIC_1M if (chosen.method == lj.METHOD_VL and not chosen.newton3 and
-                                     chosen.threads_per_unit == 2 and n == 1048576) else None
+    base = "-".join(chosen_name.split("-")[:3])
+    traffic = VL_T2_TRAFFIC_1M["bytes"] if (base == VL_T2_TRAFFIC_1M["config"] and chosen.csf == 1.0 and
+                                            n == 1048576) else None
     roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": (achieved / fp32_peak) if achieved else None, "traffic": traffic,
-            "binding_unit": "L1 gather throughput (84 % of peak in ncu, VL two lanes); DRAM 45 %, issue 48 %",
-            "kernel": "force (%s)" % chosen_name, "launch_ms": force_ms, "flops_per_launch": npairs * FLOPS_PER_PAIR,
-            "peak_basis": "152 SMs x 128 FP32 lanes x 2 x %g MHz (of measured max clock)" % sm_max}
+            "traffic_source": ("ncu capture of %s at N = 1,048,576" % VL_T2_TRAFFIC_1M["config"]) if traffic else None,
+            "kernel": "force (%s)" % chosen_name, "launch_ms": force_ms,
+            "flops_per_launch": npairs * FLOPS_PER_PAIR, "peak_basis": "of measured (FP32 probe)"}
+    # ---- step roofline -------------------------------------------------------
+    rl = 2.5 + sc["skin"]
+    entries_alg = npairs * (rl / 2.5) ** 3  # unordered pairs within the list radius
+    nc1 = int((sc["box"][0] / (rl * (1 + 1.0 / 4096) ** 2)))
+    rebuild_every = steps_done / max(run["rebuilds"], 1)
+    sr = step_roofline(n, npairs, True, entries_alg, nc1 ** 3, rebuild_every, peaks, hbm)
+    ms_step = ms / max(steps_done, 1)
+    sr["t_measured_us"] = 1e3 * ms_step
+    sr["frac"] = sr["t_roof_us"] / sr["t_measured_us"]
+    best = L["best"]
+    tuned_med = statistics.median(L["tuned_values"])
+    comparison = None
+    if best:
+        comparison = {"tuned_median": tuned_med, "best_fixed": best["name"], "best_fixed_median": best["value"],
+                      "ratio": tuned_med / best["value"], "repeats": args.repeats, "steps": K}
     cb = None
     if args.cpu_baseline and world == 1:
         cb = oracle_rate(sc)
-    adj = adjoint_leg() if args.adjoint else None
-    bat = batch_leg() if args.batch else None
-    inh = inhomogeneous_leg(fixed_steps=args.inhomo_fixed_steps) if args.inhomo else None
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": int(steps_done),
-        "warmup": W, "ms_per_step": ms / max(steps_done, 1), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "lj_liquid_1m: N=1048576 fcc 64^3x4, rho 0.8442, T 0.72, rc 2.5, skin 0.3, R 10",
-                   "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (state + lists > 129 MB)",
-                   "tuned": bool(args.tune), "chosen": chosen_name,
-                   "precision": "FP32 pair math, FP64 integration and sums"},
-        "roofline": roof,
-        "cpu_baseline": cb,
-        "e2e": e2e,
-        "clocks": clocks,
-        "gpu_launches": None,
-        "kernel_ms": {k: prof[k] for k in ("rebuild_ms", "force_ms", "update_ms", "control_ms")},
-        "pairs_within_cutoff": npairs,
-        "rebuilds": run["rebuilds"], "early_rebuilds": run["early"],
-        "tuner": dict(rep, strategy=headline) if rep else None,
-        "other_tuned_runs": extra_runs,
-        "fixed": fixed,
-        "best_fixed": max(fixed.items(), key=lambda kv: kv[1]) if fixed else None,
-        "adjoint": adj,
-        "batch": bat,
-        "inhomogeneous": inh,
-    }
-    # kernels launched in the timed region.  Graph steps: the force (and
+    details = {"peaks_probe": peaks, "hbm_gbs": hbm, "fixed": L["fixed"], "fixed_pair_efficiency": L["fixed_eff"],
+               "best_fixed": best, "tuned_values": L["tuned_values"], "other_tuned_runs": L["extra_runs"],
+               "tuner": dict(rep, strategy=L["headline"]) if rep else None,
+               "kernel_ms": {k: prof[k] for k in ("rebuild_ms", "force_ms", "update_ms", "control_ms")},
+               "counters": cnt, "pairs_within_cutoff": npairs, "rebuilds": run["rebuilds"],
+               "early_rebuilds": run["early"], "step_roofline": sr}
+    if args.adjoint:
+        details["adjoint"] = adjoint_leg()
+    if args.batch:
+        details["batch"] = batch_leg(peaks)
+    if args.inhomo:
+        details["inhomogeneous"] = inhomogeneous_leg(fixed_steps=args.inhomo_fixed_steps)
+    # kernels launched in the timed region.  Graph steps: the force (and the
     # update when N3L is on) and the control kernel, the rebuild chain when a
     # rebuild runs, and the loop-init and command kernels of each call.
     # Tuning trials run as plain launches: every trial step launches the
     # whole chain (its kernels return at once unless a rebuild is due), and
-    # each trial first builds its structure.  Chain lengths are the chosen
-    # configuration's (trials of other methods differ by one or two kernels).
+    # each trial first builds its structure.  A phase also launches its three
+    # statistics kernels.
     n3 = 1 if chosen.newton3 else 0
     chain = 5 + {lj.METHOD_VL: 1, lj.METHOD_CLUSTER: 2, lj.METHOD_VLW: 2}.get(chosen.method, 0)
     trial_steps = rep["trial_steps_total"] if rep else 0
     ntrial = rep["ntrialled"] if rep else 0
     graph_steps = steps_done - trial_steps
-    graph_rebuilds = max(0, run["rebuilds"] - ntrial - 1)
-    line["gpu_launches"] = int(trial_steps * (chain + 2 + n3) + ntrial * (chain + 3) +
-                               graph_steps * (2 + n3) + graph_rebuilds * chain + 4)
+    graph_rebuilds = max(0, run["rebuilds"] - ntrial)
+    launches = int(trial_steps * (chain + 2 + n3) + ntrial * (chain + 3) + graph_steps * (2 + n3) +
+                   graph_rebuilds * chain + 4 + (3 if rep else 0))
+    path = args.details
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    with open(path, "w") as f:
+        json.dump(details, f, indent=1, default=str)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": int(steps_done),
+        "warmup": W, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (state + lists > 129 MB)", "tuned": bool(args.tune),
+                   "strategy": L["headline"], "chosen": chosen_name,
+                   "precision": "FP32 pair math, FP64 integration and sums"},
+        "roofline": roof,
+        "step_roofline": {"t_roof_us": sr["t_roof_us"], "t_measured_us": sr["t_measured_us"], "frac": sr["frac"]},
+        "tuned_vs_best_fixed": comparison,
+        "cpu_baseline": cb,
+        "e2e": L["e2e"],
+        "clocks": L["clocks"],
+        "gpu_launches": launches,
+        "details": os.path.relpath(path, ROOT),
+    }
     print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
 
 
 def main():
@@ -556,20 +648,23 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-tune", dest="tune", action="store_false")
-    ap.add_argument("--method", default=None, help="with --no-tune: run this fixed method (LC, VL, VLW, CL)")
+    ap.add_argument("--method", default=None, help="run this fixed method (LC, VL, VLW, CL) from the start")
     ap.add_argument("--newton3", action="store_true")
     ap.add_argument("--tpu", type=int, default=1)
-    ap.add_argument("--cluster", type=int, default=8)
+    ap.add_argument("--cluster", type=int, default=4)
     ap.add_argument("--csf", type=float, default=1.0, help="with --method: cell size factor (1.0 or 0.5)")
     ap.add_argument("--trial-steps", type=int, default=5)
     ap.add_argument("--probe-steps", type=int, default=2)
     ap.add_argument("--strategy", default="forest", choices=["full", "predictive", "expert", "forest"],
-                    help="tuning strategy of the headline run (the others of expert/full/forest are reported beside it)")
+                    help="tuning strategy of the headline run (the others are reported in the details)")
+    ap.add_argument("--repeats", type=int, default=3,
+                    help="tuned runs and re-runs of the three best fixed configurations for the medians")
     ap.add_argument("--fixed-steps", type=int, default=-1, help="steps per fixed configuration (-1: same as --steps)")
     ap.add_argument("--profile-steps", type=int, default=60)
+    ap.add_argument("--details", default=os.path.join(ROOT, "_build", "bench_details.json"))
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--eager", action="store_true", help="plain stream launches instead of the step graph")
-    ap.add_argument("--no-other", dest="other", action="store_false", help="skip the second tuning strategy")
+    ap.add_argument("--no-other", dest="other", action="store_false", help="skip the other tuning strategies")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-adjoint", dest="adjoint", action="store_false", help="skip the gradient-workload timings")
     ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the batched-replica run")
@@ -578,14 +673,16 @@ def main():
                     help="screening steps per fixed configuration in the heated-sphere comparison (default 1000; "
                          "the best five then run all 20000 steps)")
     ap.add_argument("--leg", default="all", choices=["all", "batch", "adjoint", "inhomo"],
-                    help="run only the batched-replica or the gradient leg (profiling aid) and print its JSON")
+                    help="run only one leg and print its JSON")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
     elif args.leg == "batch":
-        print(json.dumps(batch_leg(steps=args.steps, warmup=args.warmup, eager=args.eager)), flush=True)
+        import paper_2505_03438_gb300 as lj
+        print(json.dumps(batch_leg(lj.ljsel_measure_peaks(30.0), steps=args.steps, warmup=args.warmup,
+                                   eager=args.eager)), flush=True)
     elif args.leg == "adjoint":
         print(json.dumps(adjoint_leg()), flush=True)
     elif args.leg == "inhomo":

@@ -150,10 +150,10 @@ typedef struct ljsel_tuner_opts {
                                   CSF-1 bin, Sec. 4 statistics); 3: random
                                   forest (the forest installed with
                                   ljsel_set_forest ranks its configurations
-                                  from the Sec. 4 statistics; the forest_top
-                                  most probable are trialled; with forest_top
-                                  1 and the first choice already in use, the
-                                  phase keeps it without a trial)             */
+                                  from the Sec. 4 statistics; with forest_top
+                                  1 its first choice is selected without a
+                                  trial, with forest_top k > 1 the k most
+                                  probable are trialled)                      */
     int32_t trial_steps;       /* steps per trial (>= 1); a trial first
                                   rebuilds, then advances trial_steps steps   */
     double predict_factor;     /* predictive: trial configs predicted within
@@ -168,9 +168,8 @@ typedef struct ljsel_tuner_opts {
                                   cost is above probe_factor x the best cost
                                   of the phase so far, the trial stops there
                                   (0: always run trial_steps)                 */
-    int32_t forest_top;        /* random forest: configurations trialled per
-                                  phase, most probable first (>= 1; 0 counts
-                                  as 1)                                       */
+    int32_t forest_top;        /* random forest: 1 (or 0): select the first
+                                  choice; k > 1: trial the k most probable  */
     double probe_factor;       /* e.g. 2.0                                     */
     double skip_within;        /* > 0: when the live statistics (mean,
                                   relative std and max particles per CSF-1
@@ -233,9 +232,12 @@ ljsel_status ljsel_create(const ljsel_params *params, int64_t n, const double *p
 
 ljsel_status ljsel_destroy(ljsel_system s);
 
-/* Select the algorithmic configuration used from now on (Sec. 2.2).  The
- * next force evaluation rebuilds the neighbour structure.  Returns
- * LJSEL_ERR_UNSUPPORTED for combinations the library does not provide.     */
+/* Select the algorithmic configuration used from now on (Sec. 2.2).  When
+ * the new configuration shares the built neighbour structure (it differs
+ * only in threads_per_unit or rebuild_interval) the structure is kept and
+ * the new interval counts from the last rebuild; otherwise the next force
+ * evaluation rebuilds.  Returns LJSEL_ERR_UNSUPPORTED for combinations the
+ * library does not provide.                                               */
 ljsel_status ljsel_set_config(ljsel_system s, const ljsel_config *cfg);
 ljsel_status ljsel_get_config(ljsel_system s, ljsel_config *cfg);
 
@@ -294,9 +296,10 @@ ljsel_status ljsel_get_stats(ljsel_system s, ljsel_stats *st);
 ljsel_status ljsel_get_counters(ljsel_system s, ljsel_counters *c);
 
 /* Run one tuning phase (Sec. 2.2.5, Sec. 5.1): trial candidate
- * configurations, each for opts->trial_steps steps that advance the
- * simulation, keep the one with the lowest cost per step (build time over
- * R plus force and integration time per step), and select it.  chosen and
+ * configurations, each building its own neighbour structure and then
+ * advancing opts->trial_steps steps of the simulation, keep the one with
+ * the lowest cost per step (build time over R plus force and integration
+ * time per step), and select it.  chosen and
  * report may be NULL.  State (blacklist, history for the predictive
  * strategy) persists across phases of the same handle.                    */
 ljsel_status ljsel_autotune(ljsel_system s, const ljsel_tuner_opts *opts,
@@ -506,6 +509,26 @@ ljsel_status ljsel_batch_autotune(ljsel_batch b, int32_t trial_steps, int32_t nc
  * 50 ns each) and records a timeout, which the host reads.  Returns
  * LJSEL_ERR_TIMEOUT when the path works; the GPU context stays usable.    */
 ljsel_status ljsel_selftest_wait_timeout(int64_t polls);
+
+/* Measured throughput of the arithmetic pipes the kernels use, in 1e12
+ * operations per second: FP32 fused multiply-add counted as 2 flops, the
+ * packed FP32x2 form counted as 4, FP64 fused multiply-add as 2, and the
+ * approximate FP32 reciprocal as 1.  The paper has no counterpart; these are
+ * the peaks that the force (FP32, reciprocal) and update (FP64) kernels are
+ * measured against.                                                         */
+typedef struct ljsel_peaks {
+    double fp32_tflops;
+    double fp32x2_tflops;
+    double fp64_tflops;
+    double rcp_tops;
+} ljsel_peaks;
+
+/* Run the four probes on the current device, each an independent-chain
+ * kernel over a grid that fills every SM, timed with CUDA events after a
+ * warm-up launch and scaled to last about target_ms (0 < target_ms <=
+ * 10000).  Allocates a small scratch buffer; synchronizes the device's
+ * legacy default stream.                                                  */
+ljsel_status ljsel_measure_peaks(double target_ms, ljsel_peaks *out);
 
 /* Allocation-free force evaluation.  The paper has no counterpart: this is
  * a service for callers that cannot allocate device memory -- code inside a

@@ -158,6 +158,10 @@ class ljsel_batch_tile(ctypes.Structure):
         return (self.threads_per_particle, self.block_threads, self.persistent_ctas_per_sm, self.rebuild_interval)
 
 
+class ljsel_peaks(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("fp32_tflops", "fp32x2_tflops", "fp64_tflops", "rcp_tops")]
+
+
 _P = ctypes.c_void_p
 _SIGS = {
     "ljsel_last_error": ([], ctypes.c_char_p),
@@ -215,6 +219,7 @@ _SIGS = {
     "ljsel_set_forest": ([_P, ctypes.POINTER(ljsel_forest)], ctypes.c_int),
     "ljsel_tuner_costs": ([_P, ctypes.c_int32, ctypes.POINTER(ljsel_config), _P, _P, ctypes.POINTER(ctypes.c_int32)],
                           ctypes.c_int),
+    "ljsel_measure_peaks": ([ctypes.c_double, ctypes.POINTER(ljsel_peaks)], ctypes.c_int),
 }
 EXPORTED = tuple(_SIGS)
 _lib = None
@@ -429,6 +434,14 @@ def ljsel_compute_forces_noalloc(params: ljsel_params, n, pos, forces, types=Non
     _check(lib().ljsel_compute_forces_noalloc(ctypes.byref(params), int(n), pp, tp, fp, ctypes.byref(e),
                                               ctypes.byref(w), stream))
     return e.value, w.value
+
+
+def ljsel_measure_peaks(target_ms=30.0) -> dict:
+    """Measured FP32 / packed FP32x2 / FP64 fused multiply-add rates (TFLOP/s)
+    and the FP32 reciprocal rate (Tops/s) of the current device."""
+    p = ljsel_peaks()
+    _check(lib().ljsel_measure_peaks(ctypes.c_double(target_ms), ctypes.byref(p)))
+    return {k: getattr(p, k) for k, _ in p._fields_}
 
 
 def ljsel_default_candidates(h):

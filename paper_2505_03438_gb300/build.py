@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libljsel.so")
-SOURCES = ["rebuild.cu", "force.cu", "cluster.cu", "window.cu", "system.cu", "capi.cu", "noalloc.cu", "adjoint.cu", "batch.cu"]
+SOURCES = ["rebuild.cu", "force.cu", "cluster.cu", "window.cu", "system.cu", "capi.cu", "noalloc.cu", "adjoint.cu", "batch.cu", "probe.cu"]
 HEADERS = ["ljsel_internal.cuh", "kernels.cuh", "system.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

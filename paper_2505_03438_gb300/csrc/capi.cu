@@ -53,6 +53,85 @@ __global__ void k_bin_counts(const double *X, int n, BinGrid g, int *counts) {
     atomicAdd(&counts[(c[2] * g.nb[1] + c[1]) * g.nb[0] + c[0]], 1);
 }
 
+// Live statistics on the device (Sec. 4): bin counts from the FP64 state
+// (wrapped into the box as ljsel_get_state wraps it), then a histogram of the
+// count values with exact integer sums, then one block that reads the mean,
+// variance, median, maximum and empty bins off the histogram.  Counts of
+// STATS_HMAX or more flag the host path (a copy of all counts).
+constexpr int STATS_HMAX = 4096;
+struct StatsAcc {
+    unsigned long long sum_sq;  // sum over bins of count^2
+    unsigned int max;
+    unsigned int overflow;      // some count >= STATS_HMAX
+};
+
+template <typename R> __global__ void k_stats_bin(Dev<R> S, BinGrid g, int *counts) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S.n) return;
+    const int sp = S.ctrl->state_par, n = S.n;
+    int c[3];
+    for (int d = 0; d < 3; ++d) {
+        double x = S.x[sp][d * n + i];
+        if (!S.walls[d]) {
+            const double L = S.boxd[d];
+            if (x < 0.0) x += L;
+            if (x >= L) x -= L;
+            if (x < 0.0 || x >= L) { x = x - L * floor(x / L); if (x >= L) x = 0.0; }
+        }
+        long long k = (long long)floor(x / g.side[d]);
+        k %= g.nb[d];
+        if (k < 0) k += g.nb[d];
+        c[d] = (int)k;
+    }
+    atomicAdd(&counts[(c[2] * g.nb[1] + c[1]) * g.nb[0] + c[0]], 1);
+}
+
+__global__ void k_stats_hist(const int *counts, long long nbins, int *hist, StatsAcc *acc) {
+    unsigned long long sq = 0;
+    unsigned int mx = 0, over = 0;
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nbins; b += (long long)gridDim.x * blockDim.x) {
+        const unsigned int c = (unsigned int)counts[b];
+        sq += (unsigned long long)c * c;
+        mx = c > mx ? c : mx;
+        if (c < (unsigned int)STATS_HMAX) atomicAdd(&hist[c], 1);
+        else over = 1;
+    }
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    over = __reduce_or_sync(0xffffffffu, over);
+    if ((threadIdx.x & 31) == 0) {
+        if (sq) atomicAdd(&acc->sum_sq, sq);
+        if (mx) atomicMax(&acc->max, mx);
+        if (over) atomicOr(&acc->overflow, over);
+    }
+}
+
+// out[0] mean, [1] rel_std, [2] median, [3] max, [4] nempty; [5] 1 if the
+// histogram overflowed (then out is not valid).
+__global__ void k_stats_final(const int *hist, const StatsAcc *acc, long long nbins, long long n, double *out) {
+    if (threadIdx.x != 0) return;
+    if (acc->overflow) { out[5] = 1.0; return; }
+    const double mean = (double)n / (double)nbins;
+    // variance = (nbins sum c^2 - n^2) / nbins^2, the numerator exact in integers
+    const __int128 num = (__int128)acc->sum_sq * nbins - (__int128)n * n;
+    const double var = (double)num / ((double)nbins * (double)nbins);
+    auto kth = [&](long long k) {
+        long long cum = 0;
+        for (int v = 0; v < STATS_HMAX; ++v) {
+            cum += hist[v];
+            if (cum > k) return v;
+        }
+        return STATS_HMAX - 1;
+    };
+    const double med = (nbins % 2) ? (double)kth(nbins / 2) : 0.5 * ((double)kth(nbins / 2 - 1) + (double)kth(nbins / 2));
+    out[0] = mean;
+    out[1] = mean > 0 ? sqrt(var > 0 ? var : 0.0) / mean : 0.0;
+    out[2] = med;
+    out[3] = (double)acc->max;
+    out[4] = (double)hist[0];
+    out[5] = 0.0;
+}
+
 // Self-test of the bounded device wait: one thread waits on a flag nothing
 // sets, gives up after `polls` polls and records a timeout.
 __global__ void k_selftest_wait(Ctrl *C, const unsigned long long *flag, int polls) {
@@ -84,6 +163,15 @@ bool same_cfg(const ljsel_config &a, const ljsel_config &b) {
     return a.method == b.method && a.newton3 == b.newton3 && a.threads_per_unit == b.threads_per_unit &&
            a.rebuild_interval == b.rebuild_interval && a.csf == b.csf &&
            (a.method != LJSEL_METHOD_CLUSTER || a.cluster_size == b.cluster_size);
+}
+
+// Two configurations use the same neighbour structure when they differ
+// only in lanes per unit or in the rebuild interval: the cell grid, the
+// sort and the lists do not depend on either.
+bool same_structure(const ljsel_config &a, const ljsel_config &b) {
+    if (a.method != b.method || a.csf != b.csf) return false;
+    if (a.method == LJSEL_METHOD_LC) return true;
+    return a.newton3 == b.newton3 && (a.method != LJSEL_METHOD_CLUSTER || a.cluster_size == b.cluster_size);
 }
 
 std::vector<ljsel_config> default_candidates(const System &s) {
@@ -383,6 +471,11 @@ ljsel_status ljsel_set_config(ljsel_system h, const ljsel_config *cfg) {
     ljsel_config c = *cfg;
     if (c.method != LJSEL_METHOD_CLUSTER) c.cluster_size = 1;
     const ljsel_config old = s->cfg;
+    // a built structure that the new configuration shares is kept (the
+    // Verlet-list guarantee of Sec. 2.2.1 depends on the positions, not on
+    // the lanes per unit or the interval); the new interval applies from
+    // the current count of steps since the last rebuild
+    const bool keep = !s->structure_dirty && same_structure(old, c);
     s->cfg = c;
     // with N3L the force buffer accumulates and must start at zero; without
     // it a force evaluation leaves its result there
@@ -396,7 +489,12 @@ ljsel_status ljsel_set_config(ljsel_system h, const ljsel_config *cfg) {
             return LJSEL_OK;
         }));
     }
-    return s->apply_config();
+    TRY(s->apply_config());
+    if (keep) {
+        s->structure_dirty = false;
+        TRY(s->cmd(CMD_INTERVAL, c.rebuild_interval));
+    }
+    return LJSEL_OK;
 }
 
 ljsel_status ljsel_get_config(ljsel_system h, ljsel_config *cfg) {
@@ -625,70 +723,71 @@ ljsel_status ljsel_get_stats(ljsel_system h, ljsel_stats *st) {
         g.side[d] = s->params.box[d] / g.nb[d];
         nbins *= g.nb[d];
     }
-    const size_t nbytes = (size_t)s->n * 3 * sizeof(double);
-    TRY(s->b_stats.ensure(nbytes + (size_t)nbins * 4));
-    if (s->h_stats_cap < (size_t)nbins) {
+    // device buffer: counts | histogram | accumulators | results
+    const size_t cbytes = ((size_t)nbins * 4 + 255) & ~(size_t)255;
+    const size_t hbytes = (size_t)STATS_HMAX * 4;
+    TRY(s->b_stats.ensure(cbytes + hbytes + 256 + 64));
+    int *counts = (int *)s->b_stats.ptr;
+    int *hist = (int *)((char *)s->b_stats.ptr + cbytes);
+    StatsAcc *acc = (StatsAcc *)((char *)s->b_stats.ptr + cbytes + hbytes);
+    double *dres = (double *)((char *)s->b_stats.ptr + cbytes + hbytes + 256);
+    const size_t hneed = std::max<size_t>(64, (size_t)nbins * 4);
+    if (s->h_stats_cap * 4 < hneed) {
         if (s->h_stats) cudaFreeHost(s->h_stats);
         s->h_stats = nullptr;
         s->h_stats_cap = 0;
-        CK(cudaMallocHost((void **)&s->h_stats, (size_t)nbins * 4));
-        s->h_stats_cap = (size_t)nbins;
+        CK(cudaMallocHost((void **)&s->h_stats, hneed));
+        s->h_stats_cap = hneed / 4;
     }
-    double *dpos = (double *)s->b_stats.ptr;
-    int *counts = (int *)((char *)s->b_stats.ptr + nbytes);
+    CK(cudaMemsetAsync(s->b_stats.ptr, 0, cbytes + hbytes + 256, s->stream));
     ljsel_status rs = dispatch(s, [&](auto z) -> ljsel_status {
         using R = decltype(z);
         Dev<R> S;
         s->fill_dev(S);
-        launch_export_state(S, dpos, nullptr, 1, s->stream);
+        k_stats_bin<R><<<div_up(s->n, 256), 256, 0, s->stream>>>(S, g, counts);
         return LJSEL_OK;
     });
     if (rs != LJSEL_OK) return rs;
-    CK(cudaMemsetAsync(counts, 0, nbins * 4, s->stream));
-    k_bin_counts<<<div_up(s->n, 256), 256, 0, s->stream>>>(dpos, s->n, g, counts);
+    k_stats_hist<<<(int)std::min<long long>(div_up(nbins, 256), 1024), 256, 0, s->stream>>>(counts, nbins, hist, acc);
+    k_stats_final<<<1, 32, 0, s->stream>>>(hist, acc, nbins, s->n, dres);
     CK(cudaGetLastError());
-    const int *hc = s->h_stats;
-    CK(cudaMemcpyAsync(s->h_stats, counts, nbins * 4, cudaMemcpyDeviceToHost, s->stream));
+    double *hres = (double *)s->h_stats;
+    CK(cudaMemcpyAsync(hres, dres, 6 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
-    const double mean = (double)s->n / (double)nbins;
-    double var = 0;
-    int mx = 0;
-    long long nempty = 0;
-    for (long long b = 0; b < nbins; ++b) {
-        double d = hc[b] - mean;
-        var += d * d;
-        mx = std::max(mx, hc[b]);
-        nempty += hc[b] == 0;
-    }
-    var /= (double)nbins;
-    // median: the counts are small integers, so their sorted order is read
-    // off a histogram of the values instead of sorting the bins
-    // (a collapse into a few bins with millions each takes a selection on a
-    // copy instead)
-    std::vector<long long> hist(mx <= (1 << 22) ? (size_t)mx + 1 : 0, 0);
-    std::vector<int> copy;
-    if (hist.empty()) copy.assign(hc, hc + nbins);
-    else
-        for (long long b = 0; b < nbins; ++b) ++hist[hc[b]];
-    auto kth = [&](long long k) {  // value of rank k (0-based) in ascending order
-        if (hist.empty()) {
+    double mean = hres[0], rel_std = hres[1], median = hres[2], mx = hres[3], nempty = hres[4];
+    if (hres[5] != 0.0) {
+        // a count of STATS_HMAX or more: every count to the host, the median
+        // by selection on a copy
+        const int *hc = s->h_stats;
+        CK(cudaMemcpyAsync(s->h_stats, counts, nbins * 4, cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        mean = (double)s->n / (double)nbins;
+        double var = 0;
+        int m = 0;
+        long long ne = 0;
+        for (long long b = 0; b < nbins; ++b) {
+            const double d = hc[b] - mean;
+            var += d * d;
+            m = std::max(m, hc[b]);
+            ne += hc[b] == 0;
+        }
+        var /= (double)nbins;
+        std::vector<int> copy(hc, hc + nbins);
+        auto kth = [&](long long k) {
             std::nth_element(copy.begin(), copy.begin() + k, copy.end());
             return copy[k];
-        }
-        long long acc = 0;
-        for (int v = 0; v <= mx; ++v) {
-            acc += hist[v];
-            if (acc > k) return v;
-        }
-        return mx;
-    };
-    const double median = (nbins % 2) ? (double)kth(nbins / 2) : 0.5 * ((double)kth(nbins / 2 - 1) + (double)kth(nbins / 2));
+        };
+        median = (nbins % 2) ? (double)kth(nbins / 2) : 0.5 * ((double)kth(nbins / 2 - 1) + (double)kth(nbins / 2));
+        rel_std = mean > 0 ? std::sqrt(var) / mean : 0.0;
+        mx = m;
+        nempty = (double)ne;
+    }
     st->mean = mean;
-    st->rel_std = mean > 0 ? std::sqrt(var) / mean : 0.0;
+    st->rel_std = rel_std;
     st->median = median;
     st->max = mx;
     st->nbins = (double)nbins;
-    st->nempty = (double)nempty;
+    st->nempty = nempty;
     st->skin = s->params.skin;
     // the counterpart of the paper's thread count: the threads the GPU keeps
     // resident (SMs x threads per SM), a property of the device, not of the
@@ -897,14 +996,20 @@ ljsel_status ljsel_autotune(ljsel_system h, const ljsel_tuner_opts *opts, ljsel_
         }
         if (!taken) trial[rank[0]] = 1;  // everything blacklisted: keep the forest's first choice
         expert_x = proba[rank[0]];
-        // one suggestion, and it is the configuration in use: nothing to
-        // decide, so the phase keeps it without a trial
-        if (top == 1 && same_cfg(cands[rank[0]], s->cfg)) {
+        // one suggestion (the paper's forest suggests a configuration): it is
+        // selected without a trial, keeping the neighbour structure when the
+        // configuration in use shares it
+        if (top == 1) {
+            const int k = rank[0];
+            if (!same_cfg(cands[k], s->cfg)) {
+                ljsel_status sc = ljsel_set_config(h, &cands[k]);
+                if (sc != LJSEL_OK) return sc;
+            }
             ljsel_tuner_report r{};
             s->tuner_phase += 1;
             r.phase = s->tuner_phase;
-            r.chosen_index = rank[0];
-            const auto &hs = ent[rank[0]]->history;
+            r.chosen_index = k;
+            const auto &hs = ent[k]->history;
             r.chosen_cost_ms = hs.empty() ? 0.0 : hs.back().second;
             r.expert_input = expert_x;
             r.phase_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -958,6 +1063,9 @@ ljsel_status ljsel_autotune(ljsel_system h, const ljsel_tuner_opts *opts, ljsel_
         ljsel_status sc = ljsel_set_config(h, &cands[k]);
         if (sc == LJSEL_ERR_UNSUPPORTED) { ent[k]->blacklisted = true; continue; }
         TRY(sc);
+        // every trial builds its own structure, so that the trials' costs
+        // compare (a shared structure would reach later trials aged)
+        s->structure_dirty = true;
         int done_steps = 0;
         ljsel_status st = dispatch(s, [&](auto z) -> ljsel_status {
             using R = decltype(z);

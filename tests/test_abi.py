@@ -50,7 +50,7 @@ def test_struct_layouts_match_header(built):
     #include "ljsel.h"
     int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(ljsel_params), sizeof(ljsel_config),
       sizeof(ljsel_stats), sizeof(ljsel_counters), sizeof(ljsel_tuner_opts), sizeof(ljsel_tuner_report),
-      sizeof(ljsel_profile));return 0;}
+      sizeof(ljsel_profile));printf("%zu\n", sizeof(ljsel_peaks));return 0;}
     '''
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "s.c")
@@ -60,7 +60,7 @@ def test_struct_layouts_match_header(built):
         out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
     sizes = [ctypes.sizeof(t) for t in (built.ljsel_params, built.ljsel_config, built.ljsel_stats,
                                         built.ljsel_counters, built.ljsel_tuner_opts, built.ljsel_tuner_report,
-                                        built.ljsel_profile)]
+                                        built.ljsel_profile, built.ljsel_peaks)]
     assert [int(s) for s in out] == sizes
 
 

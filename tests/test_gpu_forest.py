@@ -1,7 +1,8 @@
 """The Random Forest strategy (Sec. 5.3) on the GPU with the shipped forest:
-each phase trials exactly the forest_top configurations the forest ranks
-first for the live statistics (computed here from the same statistics with
-the numpy forest), keeps the cheapest of those trials, and its trial steps
+with forest_top 1 a phase selects the configuration the forest ranks first
+for the live statistics (computed here from the same statistics with the
+numpy forest) without a trial; with forest_top k > 1 it trials exactly the
+k first-ranked configurations and keeps the cheapest; the trial steps
 advance the simulation on the oracle's FP64 trajectory."""
 import numpy as np
 import pytest
@@ -30,9 +31,7 @@ def test_forest_strategy_trials_the_forests_first_choices():
     assert e.value.status == 8  # LJSEL_ERR_STATE: no forest installed
     m = forest.load()
     s.set_forest(m)
-    trialled = kept = 0
-    # two single-suggestion phases in a row: the second finds the first's
-    # choice in use (four steps barely move the statistics) and keeps it
+    trialled = selected = 0
     for phase, top in enumerate((1, 1, 3, 2)):
         st = s.stats()
         p = forest.predict_proba(m, [st[k] for k in forest.FEATURES])
@@ -41,16 +40,17 @@ def test_forest_strategy_trials_the_forests_first_choices():
         c, rep = s.autotune(strategy="forest", trial_steps=4, forest_top=top)
         assert rep["expert_input"] == p.max() and rep["phase"] == phase + 1
         costs = {k: v for k, (v, ph) in lj.ljsel_tuner_costs(s.h).items() if ph == phase}
-        if top == 1 and expect[0] == before:
-            # the single suggestion is the configuration in use: kept, no trial
-            assert rep["ntrialled"] == 0 and not costs and c.name() == before == s.config().name()
-            kept += 1
+        if top == 1:
+            # the single suggestion is selected without a trial
+            assert rep["ntrialled"] == 0 and rep["trial_steps_total"] == 0 and not costs
+            assert c.name() == expect[0] == s.config().name()
+            selected += 1
             continue
         assert rep["ntrialled"] == top
         trialled += top
         assert sorted(costs) == sorted(expect)
         assert c.name() == min(costs, key=costs.get) and s.config().name() == c.name()
-    assert kept >= 1
+    assert selected == 2
     nsteps = s.counters()["steps"]
     assert nsteps == 4 * trialled
     x, v = s.state()
