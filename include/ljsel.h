@@ -373,6 +373,20 @@ ljsel_status ljsel_predictive_trials(int32_t ncand, int32_t phase, const int32_t
                                      int32_t incumbent, double predict_factor, int32_t retrial_phases,
                                      int32_t *trial);
 
+/* The Expert strategy's rating of a configuration (Sec. 2.3, Sec. 5.2), host
+ * only (no GPU, no handle): the fuzzy input is the mean particles per CSF-1
+ * bin; input terms sparse, medium, dense (trapezoids with corners
+ * (-inf, -inf, 1, 4), (1, 4, 8, 12), (8, 12, inf, inf)); output terms bad,
+ * okay, good ((-inf, -inf, 0.1, 0.4), (0.2, 0.5, 0.5, 0.8), (0.6, 0.9, inf,
+ * inf)); the rule table maps each method family and input term to an output
+ * term (Verlet lists okay / good / good, window lists bad / okay / okay,
+ * linked cells good / okay / bad, cluster lists okay / bad / bad).  Max-min
+ * inference; *out = centre of gravity of the aggregated output set sampled
+ * at 201 points of [0, 1].  A tuning phase trials configurations rated
+ * >= 0.5.  Errors: LJSEL_ERR_ARG for NULL pointers, an unknown method or a
+ * non-finite input.                                                       */
+ljsel_status ljsel_expert_suitability(const ljsel_config *cfg, double mean_per_bin, double *out);
+
 /* Advance nsteps steps with plain stream launches, a CUDA event before and
  * after every kernel class, and report mean GPU times per launch.  The
  * steps advance the simulation like ljsel_step.  Synchronizes every step;

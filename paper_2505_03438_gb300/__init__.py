@@ -220,6 +220,8 @@ _SIGS = {
     "ljsel_tuner_costs": ([_P, ctypes.c_int32, ctypes.POINTER(ljsel_config), _P, _P, ctypes.POINTER(ctypes.c_int32)],
                           ctypes.c_int),
     "ljsel_measure_peaks": ([ctypes.c_double, ctypes.POINTER(ljsel_peaks)], ctypes.c_int),
+    "ljsel_expert_suitability": ([ctypes.POINTER(ljsel_config), ctypes.c_double, ctypes.POINTER(ctypes.c_double)],
+                                 ctypes.c_int),
 }
 EXPORTED = tuple(_SIGS)
 _lib = None
@@ -434,6 +436,13 @@ def ljsel_compute_forces_noalloc(params: ljsel_params, n, pos, forces, types=Non
     _check(lib().ljsel_compute_forces_noalloc(ctypes.byref(params), int(n), pp, tp, fp, ctypes.byref(e),
                                               ctypes.byref(w), stream))
     return e.value, w.value
+
+
+def ljsel_expert_suitability(cfg: ljsel_config, mean_per_bin) -> float:
+    """The Expert strategy's rating of a configuration (host only)."""
+    out = ctypes.c_double()
+    _check(lib().ljsel_expert_suitability(ctypes.byref(cfg), ctypes.c_double(mean_per_bin), ctypes.byref(out)))
+    return out.value
 
 
 def ljsel_measure_peaks(target_ms=30.0) -> dict:

@@ -40,19 +40,6 @@ struct BinGrid {
     int nb[3];
     double side[3];
 };
-__global__ void k_bin_counts(const double *X, int n, BinGrid g, int *counts) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int c[3];
-    for (int d = 0; d < 3; ++d) {
-        long long k = (long long)floor(X[3 * i + d] / g.side[d]);
-        k %= g.nb[d];
-        if (k < 0) k += g.nb[d];
-        c[d] = (int)k;
-    }
-    atomicAdd(&counts[(c[2] * g.nb[1] + c[1]) * g.nb[0] + c[0]], 1);
-}
-
 // Live statistics on the device (Sec. 4): bin counts from the FP64 state
 // (wrapped into the box as ljsel_get_state wraps it), then a histogram of the
 // count values with exact integer sums, then one block that reads the mean,
@@ -887,6 +874,13 @@ static double expert_suitability(const ljsel_config &c, double mean_per_bin) {
         den += m;
     }
     return den > 0 ? num / den : 0.0;
+}
+
+ljsel_status ljsel_expert_suitability(const ljsel_config *c, double mean_per_bin, double *out) {
+    if (!c || !out || !std::isfinite(mean_per_bin)) { set_error("NULL argument or non-finite input"); return LJSEL_ERR_ARG; }
+    if (c->method < 0 || c->method > 3) { set_error("unknown method"); return LJSEL_ERR_ARG; }
+    *out = expert_suitability(*c, mean_per_bin);
+    return LJSEL_OK;
 }
 
 // One tuning phase.  Candidates are trialled in the order of their last
