@@ -356,6 +356,82 @@ def inhomogeneous_leg(steps=20000, every=1000, strategy="predictive", fixed_step
             "fixed": fixed, "best_fixed": best}
 
 
+def walled_leg(steps=150000, every=1000, thermo_every=100, d_t=0.1, target=100.0, strategies=("forest", "predictive")):
+    """The walled heating sphere of Sec. 6 (5497 particles in a 200^3 box with
+    reflective walls, cutoff 3, skin 0.5, R 10, dt 1e-4): every thermo_every
+    steps a velocity-scaling thermostat moves T by at most d_t towards
+    target; every `every` steps a tuning phase re-selects the configuration
+    (its trial steps count as steps).  Each strategy's run and every fixed
+    configuration run the same schedule from the same state; times are CUDA
+    events on the system's stream around the whole run."""
+    import torch
+
+    import paper_2505_03438_gb300 as lj
+    from paper_2505_03438_gb300 import scenarios
+
+    sc = scenarios.walled_heating_sphere()
+    n = len(sc["x"])
+    stream = torch.cuda.current_stream()
+
+    def schedule(s, strategy=None, phases=None):
+        done, next_tune = 0, 0
+        while done < steps:
+            if strategy and done >= next_tune:
+                c, rep = s.autotune(strategy=strategy, trial_steps=5, probe_steps=2, probe_factor=2.0)
+                done += rep["trial_steps_total"]
+                phases.append((done, c.name(), rep["ntrialled"]))
+                next_tune += every
+            k = min(thermo_every - done % thermo_every, steps - done)
+            s.step(k)
+            done += k
+            if done % thermo_every == 0:
+                s.thermostat(target, d_t)
+        return done
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b), r
+
+    out = {"workload": "walled_heating_sphere: N=%d, box 200 with reflective walls, rc 3, skin 0.5, R 10, dt 1e-4, "
+                       "thermostat every %d steps by <= %g towards T %g, re-tune every %d" %
+                       (n, thermo_every, d_t, target, every), "steps": steps}
+    for strat in strategies:
+        s = lj.System(sc, stream=stream.cuda_stream)
+        if strat == "forest":
+            s.set_forest()
+        phases = []
+        ms, done = timed(lambda: schedule(s, strat, phases))
+        t_end = s.thermostat(target, 0.0)
+        # the phases where the choice changed
+        changes = [p for k, p in enumerate(phases) if k == 0 or p[1] != phases[k - 1][1]]
+        out[strat] = {"value": n * done / (ms * 1e-3), "steps": done, "final_T": t_end,
+                      "trials": sum(p[2] for p in phases), "choice_changes": changes[:40]}
+        s.close()
+    probe = lj.System(sc)
+    cands = lj.ljsel_default_candidates(probe.h)
+    probe.close()
+    fixed = {}
+    for c in cands:
+        f = lj.System(sc, stream=stream.cuda_stream)
+        try:
+            lj.ljsel_set_config(f.h, c)
+            ms, done = timed(lambda: schedule(f))
+            fixed[c.name()] = n * done / (ms * 1e-3)
+        except lj.LjselError:
+            pass
+        finally:
+            f.close()
+    best = max(fixed.items(), key=lambda kv: kv[1]) if fixed else None
+    out.update({"fixed": fixed, "best_fixed": best,
+                "tuned_over_best_fixed": {k: out[k]["value"] / best[1] for k in strategies} if best else None})
+    return out
+
+
 def run_reference(args):
     """Reference arm: the oracle as it stands, on the host cores.  Every
     --steps step is a bounded sample (the budget scales with the requested
@@ -602,6 +678,8 @@ def emit(args, L):
         details["batch"] = batch_leg(peaks)
     if args.inhomo:
         details["inhomogeneous"] = inhomogeneous_leg(fixed_steps=args.inhomo_fixed_steps)
+    if args.walled:
+        details["walled_heating_sphere"] = walled_leg(steps=args.walled_steps)
     # kernels launched in the timed region.  Graph steps: the force (and the
     # update when N3L is on) and the control kernel, the rebuild chain when a
     # rebuild runs, and the loop-init and command kernels of each call.
@@ -672,7 +750,10 @@ def main():
     ap.add_argument("--inhomo-fixed-steps", type=int, default=None,
                     help="screening steps per fixed configuration in the heated-sphere comparison (default 1000; "
                          "the best five then run all 20000 steps)")
-    ap.add_argument("--leg", default="all", choices=["all", "batch", "adjoint", "inhomo"],
+    ap.add_argument("--no-walled", dest="walled", action="store_false", help="skip the walled heating-sphere run")
+    ap.add_argument("--walled-steps", type=int, default=60000,
+                    help="steps of the walled heating-sphere run (the paper heats for 150000)")
+    ap.add_argument("--leg", default="all", choices=["all", "batch", "adjoint", "inhomo", "walled"],
                     help="run only one leg and print its JSON")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -687,6 +768,8 @@ def main():
         print(json.dumps(adjoint_leg()), flush=True)
     elif args.leg == "inhomo":
         print(json.dumps(inhomogeneous_leg(fixed_steps=args.inhomo_fixed_steps)), flush=True)
+    elif args.leg == "walled":
+        print(json.dumps(walled_leg(steps=args.walled_steps)), flush=True)
     else:
         run_ours(args)
 

@@ -285,6 +285,29 @@ def _with_vapour(xd, box_len, rho_vapour, dmin, rng):
     return _rsa(np.full(3, 0.5 * box_len), 0.0, box_len, n_v, dmin, rng, existing=xd, inside=False)
 
 
+def walled_heating_sphere(n=5497, box_len=200.0, density=0.8442, temperature=0.1, seed=6, rc=3.0, skin=0.5,
+                          dt=1e-4, rebuild=10):
+    """The heating sphere of Sec. 6 as a synthetic input: a ball of n LJ
+    particles, the n sites of an fcc lattice at the given density nearest
+    the centre of a cubic box with reflective walls (ties in distance broken
+    by lattice order), Maxwell-Boltzmann velocities at the starting
+    temperature (zero total momentum, rescaled to it exactly).  The paper's
+    run: 5497 molecules, a 200^3 box with reflective boundaries, cutoff 3,
+    skin 0.5, rebuild interval 10, dt 1e-4, starting at T 0.1 and heated by
+    velocity scaling every 100 iterations by at most 0.1 towards T 100."""
+    rng = np.random.default_rng(seed)
+    m = int(math.ceil((2.0 * n / 4.0) ** (1.0 / 3.0))) + 2
+    lat, lbox = fcc_lattice(m, density)
+    c = lat - 0.5 * lbox
+    order = np.argsort((c * c).sum(1), kind="stable")[:n]
+    x = c[order] + 0.5 * box_len
+    v = maxwell_boltzmann(n, temperature, 1.0, rng)
+    sc = dict(name="walled_sphere_%d" % n, x=x, v=v, types=np.zeros(n, np.int32), dt=dt, skin=skin,
+              rebuild=rebuild, temperature=temperature, seed=seed, walls=(1, 1, 1))
+    sc.update(_single_type(np.full(3, box_len), rc))
+    return sc
+
+
 def training_scenarios(seed=7, dmin=0.9, rc=2.5, dt=0.005, rebuild=10):
     """Synthetic scenarios for the data behind the Random Forest strategy, of
     the paper's kinds (Sec. 5.3: uniform gases, clustered particles, a dense

@@ -102,17 +102,24 @@ def test_thermostat_matches_the_oracle(walls):
     assert np.abs(v2 - v_ref).max() < 1e-12 * np.abs(v_ref).max()
 
 
-def test_heating_in_walls_follows_the_oracle_fp64():
-    """A small walled heating run: every 50 steps the temperature moves by at
-    most 0.1 towards 3.0 (the heating-sphere protocol of Sec. 6, scaled
-    down); the FP64 trajectory stays on the oracle's."""
+HEAT_CFGS = [dict(method="VL"), dict(method="VL", newton3=True), dict(method="LC"), dict(method="LC", newton3=True),
+             dict(method="CL", cluster_size=4, threads_per_unit=4),
+             dict(method="CL", cluster_size=2, newton3=True, threads_per_unit=4)]
+
+
+@pytest.mark.parametrize("cfg", HEAT_CFGS, ids=lambda c: "-".join("%s%s" % kv for kv in c.items()))
+def test_heating_in_walls_follows_the_oracle_fp64(cfg):
+    """A small walled heating run for every method that supports walls:
+    every 50 steps the temperature moves by at most 0.1 towards 3.0 (the
+    heating-sphere protocol of Sec. 6, scaled down); the FP64 trajectory
+    stays on the oracle's."""
     x, box = scenarios.fcc_lattice(3, 0.75)
     L = box[0] + 4.0
     x = x + 2.0
     rng = np.random.default_rng(44)
     v = scenarios.maxwell_boltzmann(len(x), 0.7, 1.0, rng)
     s = lj.System(x=x, v=v, box=np.full(3, L), walls=(1, 1, 1), precision=1, dt=0.002)
-    s.set_config(method="VL", rebuild_interval=10)
+    s.set_config(rebuild_interval=10, **cfg)
     p = oracle.make_params(L, 1.0, 1.0, 2.5, True, walls=(1, 1, 1))
     xo, vo = x.copy(), v.copy()
     temps = []
@@ -124,6 +131,25 @@ def test_heating_in_walls_follows_the_oracle_fp64():
     xg, vg = s.state()
     assert np.abs(xg - xo).max() < 1e-8 and np.abs(vg - vo).max() < 1e-8
     assert temps[-1] > temps[0]
+
+
+def test_walled_heating_sphere_workload_step0():
+    """The walled heating sphere of Sec. 6 (5497 particles, cutoff 3, skin
+    0.5): pair set and FP32 forces against the oracle at the start, for the
+    linked-cell, Verlet-list and cluster-list methods."""
+    sc = scenarios.walled_heating_sphere()
+    p = oracle.make_params(sc["box"], 1.0, 1.0, 3.0, True, walls=(1, 1, 1))
+    ref = oracle.forces_cells(_f32(sc["x"]), None, p, pairs=True)
+    for cfg in (dict(method="LC"), dict(method="VL"), dict(method="CL", cluster_size=4, threads_per_unit=8)):
+        s = lj.System(sc)
+        s.set_config(rebuild_interval=10, **cfg)
+        F, e, w = s.compute()
+        pairs, cnt = s.pairs()
+        assert cnt == ref["count"]
+        assert np.array_equal(oracle.sorted_pairs(pairs), oracle.sorted_pairs(ref["pairs"]))
+        assert np.linalg.norm(F - ref["F"]) / np.linalg.norm(ref["F"]) < 1e-5
+        assert abs(e - ref["U"]) < 2e-6 * abs(ref["U"])
+        s.close()
 
 
 def test_walls_with_window_lists_are_refused():
