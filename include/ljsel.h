@@ -241,6 +241,16 @@ ljsel_status ljsel_destroy(ljsel_system s);
 ljsel_status ljsel_set_config(ljsel_system s, const ljsel_config *cfg);
 ljsel_status ljsel_get_config(ljsel_system s, ljsel_config *cfg);
 
+/* Set the capacity of the current configuration's list rows (entries per
+ * particle row for VL, rounded up to a multiple of 4; per window-list row
+ * for VLW, a multiple of 16, at most 512; per i-cluster row for CLUSTER, a
+ * multiple of 4) instead of the library's estimate, and rebuild before the
+ * next evaluation.  A build that needs more still grows the rows and
+ * rebuilds.  Errors: ARG for entries outside 4 .. 65532 (or above 512 for
+ * VLW), STATE for linked cells (no list).  The next ljsel_set_config
+ * re-estimates the capacity only when the rows must grow.                 */
+ljsel_status ljsel_set_list_capacity(ljsel_system s, int64_t entries);
+
 /* Rebuild the neighbour structure now (binning, sorting, lists; Sec.
  * 2.2.1).  Positions are wrapped into the box first.                     */
 ljsel_status ljsel_rebuild(ljsel_system s);
@@ -507,6 +517,9 @@ ljsel_status ljsel_batch_get_work_positions(ljsel_batch b, double *pos);
  * replica-local input indices; *count the total (may exceed cap).         */
 ljsel_status ljsel_batch_get_pairs(ljsel_batch b, int64_t cap, int32_t *rij, int64_t *count);
 ljsel_status ljsel_batch_get_counters(ljsel_batch b, ljsel_counters *c);
+/* Set the row capacity of the batch's lists (a multiple of 4, as for a
+ * single system's VL rows); rebuilt before the next step.                 */
+ljsel_status ljsel_batch_set_list_capacity(ljsel_batch b, int64_t entries);
 /* nsteps real steps with CUDA events around each kernel class, as
  * ljsel_profile_steps (force_ms covers the fused force + update kernel).  */
 ljsel_status ljsel_batch_profile_steps(ljsel_batch b, int64_t nsteps, ljsel_profile *out);

@@ -17,7 +17,7 @@
  *   - Sec. 2.2.1: linked cells of side r_c + skin scaled by the cell size
  *     factor (CSF) and stretched to tile the domain exactly.
  *   - Sec. 4: live statistics of particles per CSF-1 cell bin.
- * Readings where the paper is silent (all listed in the design notes):
+ * Readings where the paper is silent:
  *   - energy-shifted potential: U_s(r) = U(r) - U(r_c) for r < r_c, force
  *     unshifted;
  *   - "within r_c" is strict: a pair counts iff r^2 < r_c^2, and r^2 is
@@ -31,10 +31,9 @@
  *     and a particle that crosses a wall after a drift is mirrored back with
  *     its velocity component reversed.
  *
- * Compile with -O2 -ffp-contract=off (the build script does).  "Parity
- * unpinned" applies to nothing in this file: every routine is pinned by the
- * CPU tests against closed forms, invariants, lattice sums, a library
- * neighbour search or a second traversal.
+ * Compile with -O2 -ffp-contract=off (the build script does).  Every
+ * routine is checked on the CPU against closed forms, invariants, lattice
+ * sums, a library neighbour search or a second traversal.
  */
 #include <math.h>
 #include <stdint.h>

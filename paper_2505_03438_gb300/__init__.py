@@ -18,7 +18,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libljsel.so")
+# LJSEL_LIBRARY=checked selects the bounds-checked build (see build.py)
+LIB_PATH = os.path.join(_HERE, "_build", "libljsel_checked.so" if os.environ.get("LJSEL_LIBRARY") == "checked"
+                        else "libljsel.so")
 MAX_TYPES = 4
 
 METHOD_LC, METHOD_VL, METHOD_CLUSTER, METHOD_VLW = 0, 1, 2, 3
@@ -220,6 +222,8 @@ _SIGS = {
     "ljsel_tuner_costs": ([_P, ctypes.c_int32, ctypes.POINTER(ljsel_config), _P, _P, ctypes.POINTER(ctypes.c_int32)],
                           ctypes.c_int),
     "ljsel_measure_peaks": ([ctypes.c_double, ctypes.POINTER(ljsel_peaks)], ctypes.c_int),
+    "ljsel_set_list_capacity": ([_P, ctypes.c_int64], ctypes.c_int),
+    "ljsel_batch_set_list_capacity": ([_P, ctypes.c_int64], ctypes.c_int),
     "ljsel_expert_suitability": ([ctypes.POINTER(ljsel_config), ctypes.c_double, ctypes.POINTER(ctypes.c_double)],
                                  ctypes.c_int),
 }
@@ -436,6 +440,14 @@ def ljsel_compute_forces_noalloc(params: ljsel_params, n, pos, forces, types=Non
     _check(lib().ljsel_compute_forces_noalloc(ctypes.byref(params), int(n), pp, tp, fp, ctypes.byref(e),
                                               ctypes.byref(w), stream))
     return e.value, w.value
+
+
+def ljsel_set_list_capacity(h, entries):
+    _check(lib().ljsel_set_list_capacity(h, int(entries)))
+
+
+def ljsel_batch_set_list_capacity(b, entries):
+    _check(lib().ljsel_batch_set_list_capacity(b, int(entries)))
 
 
 def ljsel_expert_suitability(cfg: ljsel_config, mean_per_bin) -> float:

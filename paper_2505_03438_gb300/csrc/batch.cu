@@ -347,6 +347,14 @@ template <typename R> __global__ void __launch_bounds__(128) k_bvl_build(BDev<R>
         S.nl_count[q] = 0;
         return;
     }
+    {
+        // the longest row of the build (reported by the counters): one
+        // atomic per warp over the lanes still here
+        const unsigned act = __activemask();
+        const unsigned m = __reduce_max_sync(act, (unsigned)need);
+        if ((int)(threadIdx.x & 31) == __ffs(act) - 1 && m)
+            atomicMax((unsigned long long *)&C->need_cap, (unsigned long long)m);
+    }
     if (nf & 3) {
         const uint32_t sent = (uint32_t)S.ntot;
         for (int m = nf & 3; m < 4; ++m) { b3 = b2; b2 = b1; b1 = b0; b0 = sent; }
@@ -392,7 +400,8 @@ __global__ void __launch_bounds__(256) k_bforce(BDev<R> S, int2 *pairs3, long lo
             const uint32_t *row = S.nl + (size_t)i * S.nl_cap;
             const uint4 *row4 = reinterpret_cast<const uint4 *>(row);
             const int cnt = S.nl_count[i];
-            const int nq = ((cnt & 0xffff) + 3) >> 2, nb = cnt >> 16;
+            int nq = ((cnt & 0xffff) + 3) >> 2, nb = cnt >> 16;
+            if (!lj_check(4 * nq + nb <= S.nl_cap, C, CHECK_BATCH_ENTRY)) { nq = 0; nb = 0; }
             auto pair = [&](int j, int sx, int sy, int sz, R dx, R dy, R dz, const V4<R> &pj) {
                 const R r2 = r2_of(dx, dy, dz);
                 const bool in = Cut<R>::in(r2, S.rc2lo, S.rc2hi, pi, pj, sx, sy, sz, I.boxd, S.rc2d);
@@ -417,7 +426,10 @@ __global__ void __launch_bounds__(256) k_bforce(BDev<R> S, int2 *pairs3, long lo
             };
             // entries without an image: four at a time (padded with the sentinel)
             for (int k = sub; k < nq; k += G) {
-                const uint4 e = __ldg(row4 + k);
+                uint4 e = __ldg(row4 + k);
+                const unsigned nn = (unsigned)S.ntot;  // the sentinel ntot pads the front
+                if (!lj_check(e.x <= nn && e.y <= nn && e.z <= nn && e.w <= nn, C, CHECK_BATCH_ENTRY))
+                    e = make_uint4(nn, nn, nn, nn);
                 const V4<R> p0 = P[e.x], p1 = P[e.y], p2 = P[e.z], p3 = P[e.w];
                 pair((int)e.x, 0, 0, 0, pi.x - p0.x, pi.y - p0.y, pi.z - p0.z, p0);
                 pair((int)e.y, 0, 0, 0, pi.x - p1.x, pi.y - p1.y, pi.z - p1.z, p1);
@@ -428,6 +440,7 @@ __global__ void __launch_bounds__(256) k_bforce(BDev<R> S, int2 *pairs3, long lo
             for (int k = sub; k < nb; k += G) {
                 const uint32_t e = row[S.nl_cap - 1 - k];
                 const int j = (int)(e & JMASK);
+                if (!lj_check(j < S.ntot, C, CHECK_BATCH_ENTRY)) break;
                 int sx, sy, sz;
                 decode_image(e >> JBITS, sx, sy, sz);
                 const V4<R> pj = P[j];
@@ -655,6 +668,10 @@ struct ljsel_batch_s {
         CK(cudaMemcpyAsync(h_ctrl, b_ctrl.ptr, sizeof(Ctrl), cudaMemcpyDeviceToHost, stream));
         CK(cudaStreamSynchronize(stream));
         if (h_ctrl->nonfinite) { set_error("non-finite position, velocity or force"); return LJSEL_ERR_NONFINITE; }
+        if (h_ctrl->check_failed) {
+            set_error("bounds check failed at site " + std::to_string(h_ctrl->check_site) + " (checked build)");
+            return LJSEL_ERR_STATE;
+        }
         return LJSEL_OK;
     }
 
@@ -695,6 +712,16 @@ struct ljsel_batch_s {
         }
         set_error("batch neighbour lists keep overflowing");
         return LJSEL_ERR_CAPACITY;
+    }
+
+    // Row capacity set by the caller; the rows are rebuilt before the next step.
+    ljsel_status set_capacity(int cap) {
+        nl_cap = (cap + 3) & ~3;
+        TRY(b_nl.ensure((size_t)nl_cap * ntot * 4));
+        drop_graphs();
+        TRY(cmd(CMD_CLEAR, 0));
+        TRY(cmd(CMD_REBUILD, 0));
+        return LJSEL_OK;
     }
 
     ljsel_status grow() {
@@ -1224,6 +1251,12 @@ ljsel_status ljsel_batch_profile_steps(ljsel_batch b, int64_t nsteps, ljsel_prof
         out->total_ms = tr + tf + tc;
         return LJSEL_OK;
     });
+}
+
+ljsel_status ljsel_batch_set_list_capacity(ljsel_batch b, int64_t entries) {
+    if (!b) { set_error("NULL handle"); return LJSEL_ERR_ARG; }
+    if (entries < 4 || entries > 65532) { set_error("entries per row must be in 4 .. 65532"); return LJSEL_ERR_ARG; }
+    return b->set_capacity((int)entries);
 }
 
 ljsel_status ljsel_batch_get_counters(ljsel_batch b, ljsel_counters *c) {

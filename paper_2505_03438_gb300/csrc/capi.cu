@@ -484,6 +484,23 @@ ljsel_status ljsel_set_config(ljsel_system h, const ljsel_config *cfg) {
     return LJSEL_OK;
 }
 
+ljsel_status ljsel_set_list_capacity(ljsel_system h, int64_t entries) {
+    System *s = (System *)h;
+    if (!s) { set_error("NULL handle"); return LJSEL_ERR_ARG; }
+    if (entries < 4 || entries > 65532) { set_error("entries per row must be in 4 .. 65532"); return LJSEL_ERR_ARG; }
+    const int e = (int)entries;
+    switch (s->cfg.method) {
+        case LJSEL_METHOD_VL: s->nl_cap = (e + 3) & ~3; s->cap_fitted = true; break;
+        case LJSEL_METHOD_VLW:
+            if (e > 512) { set_error("window-list rows hold at most 512 entries"); return LJSEL_ERR_ARG; }
+            s->nl_cap = (e + 15) & ~15;
+            break;
+        case LJSEL_METHOD_CLUSTER: s->cp_cap = (e + 3) & ~3; break;
+        default: set_error("linked cells keep no list"); return LJSEL_ERR_STATE;
+    }
+    return s->apply_config();
+}
+
 ljsel_status ljsel_get_config(ljsel_system h, ljsel_config *cfg) {
     System *s = (System *)h;
     if (!s || !cfg) { set_error("NULL argument"); return LJSEL_ERR_ARG; }

@@ -296,6 +296,8 @@ __global__ void __launch_bounds__(CL_THREADS) k_cl(Dev<R> S, int T, int2 *pairs,
         const int cnt = S.cp_count[c];
         nf = cnt & 0xffff;
         nb = cnt >> 16;
+        if (!lj_check(fi >= 0 && ni >= 0 && ni <= M && fi + ni <= S.n, C, CHECK_CL_MEMBERS)) { fi = 0; ni = 0; nf = 0; nb = 0; }
+        if (!lj_check(((nf + 3) & ~3) + nb <= S.cp_cap, C, CHECK_CL_ROW)) { nf = 0; nb = 0; }
     }
     V4<R> pi[M];
     int ii[M], ti[M];
@@ -324,8 +326,10 @@ __global__ void __launch_bounds__(CL_THREADS) k_cl(Dev<R> S, int T, int2 *pairs,
     const uint4 *rq = reinterpret_cast<const uint4 *>(row);
     uint4 en = g < nq ? __ldg(rq + g) : make_uint4(0u, 0u, 0u, 0u);
     for (int q = g; q < nq; q += T) {
-        const uint4 e = en;
+        uint4 e = en;
         if (q + T < nq) en = __ldg(rq + q + T);
+        const unsigned nn = (unsigned)S.n;  // the sentinel n pads the front
+        if (!lj_check(e.x <= nn && e.y <= nn && e.z <= nn && e.w <= nn, C, CHECK_CL_FRONT)) e = make_uint4(nn, nn, nn, nn);
         const V4<R> p0 = ldpos(P, (int)e.x), p1 = ldpos(P, (int)e.y), p2 = ldpos(P, (int)e.z), p3 = ldpos(P, (int)e.w);
         cl_entry<R, M, N3L, MODE, EV, MT>(S, Tb, pi, ii, ti, (int)e.x, p0, 0, 0, 0, fx, fy, fz, u, w, np, sp, pairs, pcap);
         cl_entry<R, M, N3L, MODE, EV, MT>(S, Tb, pi, ii, ti, (int)e.y, p1, 0, 0, 0, fx, fy, fz, u, w, np, sp, pairs, pcap);
@@ -335,6 +339,7 @@ __global__ void __launch_bounds__(CL_THREADS) k_cl(Dev<R> S, int T, int2 *pairs,
     for (int e = g; e < nb; e += T) {
         const uint32_t ent = __ldg(row + cap - 1 - e);
         const int j = (int)(ent & JMASK);
+        if (!lj_check(j < S.n, C, CHECK_CL_BACK)) break;
         int sx, sy, sz;
         decode_image(ent >> JBITS, sx, sy, sz);
         const V4<R> pj = ldpos(P, j);
@@ -467,6 +472,8 @@ __global__ void __launch_bounds__(CL_THREADS, M == 2 ? 6 : (M == 4 ? 5 : 4)) k_c
         const int cnt = S.cp_count[c];
         nf = cnt & 0xffff;
         nb = cnt >> 16;
+        if (!lj_check(fi >= 0 && ni >= 0 && ni <= M && fi + ni <= S.n, C, CHECK_CL_MEMBERS)) { fi = 0; ni = 0; nf = 0; nb = 0; }
+        if (!lj_check(((nf + 3) & ~3) + nb <= S.cp_cap, C, CHECK_CL_ROW)) { nf = 0; nb = 0; }
     }
     float2 mx[M / 2], my[M / 2], mz[M / 2], fx[M / 2], fy[M / 2], fz[M / 2];
     // absent members sit far from the box and from the sentinel particle n
@@ -494,7 +501,9 @@ __global__ void __launch_bounds__(CL_THREADS, M == 2 ? 6 : (M == 4 ? 5 : 4)) k_c
     const uint4 *rq = reinterpret_cast<const uint4 *>(row);
     __shared__ __align__(16) float4 s_stage[2][4][CL_THREADS];
     const int tid = threadIdx.x;
-    auto issue = [&](int st, const uint4 &e) {
+    auto issue = [&](int st, uint4 e) {
+        const unsigned nn = (unsigned)S.n;  // the sentinel n pads the front
+        if (!lj_check(e.x <= nn && e.y <= nn && e.z <= nn && e.w <= nn, C, CHECK_CL_FRONT)) e = make_uint4(nn, nn, nn, nn);
         cp_async16(&s_stage[st][0][tid], P + e.x);
         cp_async16(&s_stage[st][1][tid], P + e.y);
         cp_async16(&s_stage[st][2][tid], P + e.z);
@@ -542,6 +551,7 @@ __global__ void __launch_bounds__(CL_THREADS, M == 2 ? 6 : (M == 4 ? 5 : 4)) k_c
     for (int e = g; e < nb; e += T) {
         const uint32_t ent = __ldg(row + cap - 1 - e);
         const int j = (int)(ent & JMASK);
+        if (!lj_check(j < S.n, C, CHECK_CL_BACK)) break;
         int sx, sy, sz;
         decode_image(ent >> JBITS, sx, sy, sz);
         const float4 pj = __ldg(P + j);

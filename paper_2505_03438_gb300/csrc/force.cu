@@ -154,6 +154,7 @@ __global__ void __launch_bounds__(FORCE_THREADS, 8) k_vl(Dev<R> S, int tpp, int2
         const int cnt = S.nl_count[i];
         nq = ((cnt & 0xffff) + 3) >> 2;
         nb = cnt >> 16;
+        if (!lj_check(4 * nq + nb <= S.nl_cap, C, CHECK_VL_ROW)) { nq = 0; nb = 0; }
         ti = type_of(pi);
         rowp = S.nl + (size_t)i * S.nl_cap;
     }
@@ -162,6 +163,8 @@ __global__ void __launch_bounds__(FORCE_THREADS, 8) k_vl(Dev<R> S, int tpp, int2
     uint4 e = sub < nq ? __ldg(row + sub) : make_uint4(0, 0, 0, 0);
     for (int q = sub; q < nq; q += tpp) {
         const uint4 en = q + tpp < nq ? __ldg(row + q + tpp) : e;
+        const unsigned nn = (unsigned)S.n;  // the sentinel n pads the front
+        if (!lj_check(e.x <= nn && e.y <= nn && e.z <= nn && e.w <= nn, C, CHECK_VL_FRONT)) e = make_uint4(nn, nn, nn, nn);
         const V4<R> p0 = ldpos(P, (int)e.x), p1 = ldpos(P, (int)e.y), p2 = ldpos(P, (int)e.z), p3 = ldpos(P, (int)e.w);
         vl_pair<R, N3L, MODE, EV, MT>(S, T, pi, ti, i, sp, (int)e.x, 0, 0, 0, pi.x - p0.x, pi.y - p0.y, pi.z - p0.z, p0, a, pairs, cap);
         vl_pair<R, N3L, MODE, EV, MT>(S, T, pi, ti, i, sp, (int)e.y, 0, 0, 0, pi.x - p1.x, pi.y - p1.y, pi.z - p1.z, p1, a, pairs, cap);
@@ -171,7 +174,8 @@ __global__ void __launch_bounds__(FORCE_THREADS, 8) k_vl(Dev<R> S, int tpp, int2
     }
     for (int k = sub; k < nb; k += tpp) {
         const uint32_t ent = rowp[S.nl_cap - 1 - k];
-        const int j = (int)(ent & JMASK);
+        int j = (int)(ent & JMASK);
+        if (!lj_check(j < S.n, C, CHECK_VL_BACK)) break;
         int sx, sy, sz;
         decode_image(ent >> JBITS, sx, sy, sz);
         const V4<R> pj = ldpos(P, j);
@@ -233,7 +237,9 @@ __global__ void __launch_bounds__(FORCE_THREADS) k_lc(Dev<R> S, int2 *pairs, lon
                     if (!stencil_cell(cx, ox, S.nc[0], S.walls[0], wx, sx)) continue;
                     const int cc = (wz * S.nc[1] + wy) * S.nc[0] + wx;
                     const bool img = (sx | sy | sz) != 0;
-                    const int jb = S.cell_start[cc], je = S.cell_start[cc + 1];
+                    if (!lj_check(cc >= 0 && cc < S.ncell, C, CHECK_LC_CELL)) continue;
+                    int jb = S.cell_start[cc], je = S.cell_start[cc + 1];
+                    if (!lj_check(jb >= 0 && jb <= je && je <= S.n, C, CHECK_LC_CELL)) continue;
                     // one pair; the exact image arithmetic only in image cells
                     auto one = [&](int j, R dx, R dy, R dz, const V4<R> &pj) {
                         const R r2 = r2_of(dx, dy, dz);

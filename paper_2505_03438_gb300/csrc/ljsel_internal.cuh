@@ -113,7 +113,31 @@ struct Ctrl {
     int32_t rebuild_all;       // batches: the next rebuild covers every replica
     double epot, virial, ekin; // FP64 sums
     int64_t replica_rebuilds;  // batches: replica rebuilds summed over replicas
+    int32_t check_failed;      // checked build: an index fell outside its array
+    int32_t check_site;        // checked build: the first failing site (CHECK_* code)
 };
+
+// Bounds checks of the checked build (compiled with -DLJSEL_CHECK): an index
+// outside its array is recorded in Ctrl::check_failed, with the site's code
+// in Ctrl::check_site, and the caller replaces it by a safe one, so the
+// kernel never touches memory outside its buffers; the host then reports
+// LJSEL_ERR_STATE.  In the normal build every check is true and compiles away.
+enum {
+    CHECK_VL_FRONT = 1, CHECK_VL_BACK = 2, CHECK_VL_ROW = 3, CHECK_LC_CELL = 4, CHECK_CL_ROW = 5,
+    CHECK_CL_FRONT = 6, CHECK_CL_BACK = 7, CHECK_CL_MEMBERS = 8, CHECK_VLW_SLOT = 9, CHECK_BATCH_ENTRY = 10,
+    CHECK_SORT_SLOT = 11, CHECK_BUILD_CELL = 12
+};
+#ifdef LJSEL_CHECK
+__device__ __forceinline__ bool lj_check(bool ok, Ctrl *C, int site) {
+    if (!ok) {
+        atomicExch(&C->check_failed, 1);
+        atomicCAS(&C->check_site, 0, site);
+    }
+    return ok;
+}
+#else
+__device__ __forceinline__ bool lj_check(bool, Ctrl *, int) { return true; }
+#endif
 
 // Everything a kernel needs, passed by value.
 template <typename R> struct Dev {

@@ -229,7 +229,9 @@ __global__ void k_sortgather(Dev<R> S) {
     const unsigned long long key = S.tmp_key[e];
     int rank = 0;
     for (int f = 0; f < m; ++f) rank += S.tmp_key[start + f] < key ? 1 : 0;
-    gather_one(S, sp, pp, start + rank, S.tmp_idx[e]);
+    const int src = S.tmp_idx[e];
+    if (!lj_check(start + rank < S.n && src >= 0 && src < S.n, C, CHECK_SORT_SLOT)) return;
+    gather_one(S, sp, pp, start + rank, src);
 }
 
 // Verlet-list rows, one thread per sorted particle i: all j with

@@ -404,6 +404,10 @@ ljsel_status System::read_ctrl() {
 }
 
 ljsel_status System::check_device_errors() {
+    if (h_ctrl->check_failed) {
+        set_error("bounds check failed at site " + std::to_string(h_ctrl->check_site) + " (checked build)");
+        return LJSEL_ERR_STATE;
+    }
     if (h_ctrl->nonfinite) { set_error("non-finite position, velocity or force"); return LJSEL_ERR_NONFINITE; }
     if (h_ctrl->timeout) { set_error("a bounded device wait gave up (scan look-back)"); return LJSEL_ERR_TIMEOUT; }
     if (h_ctrl->window_overflow) {

@@ -462,7 +462,8 @@ __global__ void __launch_bounds__(WTHREADS) k_vlw(Dev<R> S, int2 *pairs, long lo
                 const uint32_t wv[4] = {e.x, e.y, e.z, e.w};
 #pragma unroll
                 for (int h = 0; h < 4; ++h) {
-                    const int s0 = (int)(wv[h] & 0xffffu), s1 = (int)(wv[h] >> 16);
+                    int s0 = (int)(wv[h] & 0xffffu), s1 = (int)(wv[h] >> 16);
+                    if (!lj_check(s0 < WIN_SLOTS && s1 < WIN_SLOTS, C, CHECK_VLW_SLOT)) { s0 = WIN_CAP; s1 = WIN_CAP; }
                     const V4<R> q0 = win.pos[s0], q1 = win.pos[s1];
                     pair(s0, 0, 0, 0, pi.x - q0.x, pi.y - q0.y, pi.z - q0.z, q0);
                     pair(s1, 0, 0, 0, pi.x - q1.x, pi.y - q1.y, pi.z - q1.z, q1);

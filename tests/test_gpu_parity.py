@@ -424,3 +424,64 @@ def test_unshifted_potential_and_unequal_masses_fp64(lj):
     assert np.abs(v - vo).max() < 1e-10
     ep, ek, _ = s.energy()
     assert abs(ep - epo[-1]) < 1e-9 * abs(epo[-1]) and abs(ek - eko[-1]) < 1e-9 * abs(eko[-1])
+
+
+ROW_CFGS = [dict(method="VL"), dict(method="VL", newton3=True), dict(method="VL", csf=0.5),
+            dict(method="VL", threads_per_unit=4), dict(method="VLW"), dict(method="VLW", newton3=True),
+            dict(method="CL", cluster_size=4, threads_per_unit=4),
+            dict(method="CL", cluster_size=2, newton3=True, threads_per_unit=2)]
+
+
+@pytest.mark.parametrize("cfg", ROW_CFGS, ids=lambda c: "-".join("%s%s" % kv for kv in c.items()))
+def test_rows_ending_at_their_capacity(lj, cfg):
+    """List rows that end exactly at their capacity or within one 16-byte
+    chunk of it, with periodic-image entries at the back of the row: in a box
+    just above the smallest accepted one most rows carry image entries.  The
+    row capacity is set to the longest row of the build (rounded up to the
+    row granularity) and to one chunk more; the structure must be built
+    without growing the rows, and pair sets and forces must match the oracle
+    at the build positions and after a drift that keeps the lists."""
+    L = 2 * 2.8 * (1 + 1.0 / 1024) + 0.3
+    unit = 16 if cfg["method"] == "VLW" else 4
+    for seed in range(4):
+        sc = scenarios.random_gas(170, L, seed=300 + seed, min_dist=0.8)
+        s = lj.System(sc)
+        s.set_config(rebuild_interval=10, **cfg)
+        s.compute()
+        longest = s.counters()["longest_row"]
+        assert longest > 0
+        for cap in ((longest + unit - 1) // unit * unit, (longest + unit - 1) // unit * unit + unit):
+            s.set_state(sc["x"], sc["v"])
+            lj.ljsel_set_list_capacity(s.h, cap)
+            retries = s.counters()["capacity_retries"]
+            check_against_oracle(s, sc, sc["x"])
+            c = s.counters()
+            assert c["capacity_retries"] == retries and c["longest_row"] <= cap, (cap, c)
+            x1 = drift(sc["x"], sc["box"], 400 + seed, 0.9 * 0.5 * sc["skin"])
+            s.move_particles(x1)
+            check_against_oracle(s, sc, x1)
+        s.close()
+
+
+def test_batch_rows_ending_at_their_capacity(lj):
+    """The same for the batched replicas' rows: small boxes (about two cells
+    a side), capacity set to the longest row and to one chunk more."""
+    reps = [scenarios.random_gas(150, 5.7 + 0.05 * k, seed=320 + k, min_dist=0.8) for k in range(6)]
+    b = lj.Batch(reps)
+    b.compute()
+    longest = b.counters()["longest_row"]
+    assert longest > 0
+    for cap in ((longest + 3) // 4 * 4, (longest + 3) // 4 * 4 + 4):
+        lj.ljsel_batch_set_list_capacity(b.h, cap)
+        retries = b.counters()["capacity_retries"]
+        F, e, w = b.compute()
+        pairs = b.pairs()
+        Fr = b.split(F)
+        for r, sc in enumerate(reps):
+            ref = oracle.forces_cells(_f32(sc["x"]), None, _orc_params(sc), pairs=True)
+            mine = pairs[pairs[:, 0] == r][:, 1:]
+            assert np.array_equal(oracle.sorted_pairs(mine), oracle.sorted_pairs(ref["pairs"])), (cap, r)
+            assert np.linalg.norm(Fr[r] - ref["F"]) / np.linalg.norm(ref["F"]) <= FORCE_TOL
+        c = b.counters()
+        assert c["capacity_retries"] == retries and c["longest_row"] <= cap, (cap, c)
+    b.close()
