@@ -23,6 +23,8 @@
 // entries without a periodic image from the front, padded with the far
 // sentinel particle n to a multiple of four, entries with one (27-bit index
 // + 5-bit image code) from the back; cp_count[c] = front | back << 16.
+#include <algorithm>
+
 #include "kernels.cuh"
 #include "update.cuh"
 
@@ -51,7 +53,9 @@ template <typename R> struct CTab {
 // periodic image of a member is never within r_list of the cluster: a
 // periodic dimension has at least two cells of side >= r_list / 2 with
 // L >= 2 r_list.)  A row whose final length exceeds the capacity is
-// discarded and flagged; the host grows the rows and rebuilds.
+// discarded and flagged; the host grows the rows and rebuilds.  The grid is
+// capped (warps stride over the clusters), so that a launch that finds no
+// rebuild due costs little.
 template <typename R, int M, bool N3L, int RCH>
 __global__ void __launch_bounds__(CLB_THREADS) k_cl_build(Dev<R> S) {
     Ctrl *C = S.ctrl;
@@ -60,10 +64,10 @@ __global__ void __launch_bounds__(CLB_THREADS) k_cl_build(Dev<R> S) {
     if (threadIdx.x == 0) s_entries = 0ull;
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int c = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     const int ncl = min(*S.ncl_total, S.ncl_cap);
+    const int nwarps = (int)((gridDim.x * (unsigned)blockDim.x) >> 5);
     unsigned need = 0;
-    if (c < ncl) {
+    for (int c = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5); c < ncl; c += nwarps) {
         const V4<R> *P = S.pos[C->pos_par];
         const int fi = S.cl_first[c], ni = S.cl_count[c];
         R mx[M], my[M], mz[M];
@@ -132,7 +136,7 @@ __global__ void __launch_bounds__(CLB_THREADS) k_cl_build(Dev<R> S) {
         // the front is read in 16-byte chunks of four: pad it with the far
         // sentinel particle n, whose pairs are never in range
         const int nf4 = (nf + 3) & ~3;
-        need = (unsigned)(nf4 + nb);
+        need = max(need, (unsigned)(nf4 + nb));
         const bool fits = nf4 + nb <= cap && nf4 <= 0xffff && nb <= 0x7fff;
         if (fits && lane < nf4 - nf) row[nf + lane] = (uint32_t)S.n;
         if (lane == 0) {
@@ -324,10 +328,10 @@ __global__ void __launch_bounds__(CL_THREADS) k_cl(Dev<R> S, int T, int2 *pairs,
     const uint32_t *row = S.cp + (size_t)(cvalid ? c : 0) * cap;
     const int nq = (nf + 3) >> 2;
     const uint4 *rq = reinterpret_cast<const uint4 *>(row);
-    uint4 en = g < nq ? __ldg(rq + g) : make_uint4(0u, 0u, 0u, 0u);
+    uint4 en = g < nq ? __ldcs(rq + g) : make_uint4(0u, 0u, 0u, 0u);
     for (int q = g; q < nq; q += T) {
         uint4 e = en;
-        if (q + T < nq) en = __ldg(rq + q + T);
+        if (q + T < nq) en = __ldcs(rq + q + T);
         const unsigned nn = (unsigned)S.n;  // the sentinel n pads the front
         if (!lj_check(e.x <= nn && e.y <= nn && e.z <= nn && e.w <= nn, C, CHECK_CL_FRONT)) e = make_uint4(nn, nn, nn, nn);
         const V4<R> p0 = ldpos(P, (int)e.x), p1 = ldpos(P, (int)e.y), p2 = ldpos(P, (int)e.z), p3 = ldpos(P, (int)e.w);
@@ -337,7 +341,7 @@ __global__ void __launch_bounds__(CL_THREADS) k_cl(Dev<R> S, int T, int2 *pairs,
         cl_entry<R, M, N3L, MODE, EV, MT>(S, Tb, pi, ii, ti, (int)e.w, p3, 0, 0, 0, fx, fy, fz, u, w, np, sp, pairs, pcap);
     }
     for (int e = g; e < nb; e += T) {
-        const uint32_t ent = __ldg(row + cap - 1 - e);
+        const uint32_t ent = __ldcs(row + cap - 1 - e);
         const int j = (int)(ent & JMASK);
         if (!lj_check(j < S.n, C, CHECK_CL_BACK)) break;
         int sx, sy, sz;
@@ -519,9 +523,9 @@ __global__ void __launch_bounds__(CL_THREADS, M == 2 ? 6 : (M == 4 ? 5 : 4)) k_c
         if (N3L && j < S.n && (hx != 0.f || hy != 0.f || hz != 0.f)) atomicAdd(S.force + j, make_float4(-hx, -hy, -hz, 0.f));
     };
     uint4 e0 = make_uint4(0u, 0u, 0u, 0u), e1 = e0;
-    if (g < nq) { e0 = __ldg(rq + g); issue(0, e0); }
+    if (g < nq) { e0 = __ldcs(rq + g); issue(0, e0); }
     cp_async_commit();
-    if (g + T < nq) e1 = __ldg(rq + g + T);
+    if (g + T < nq) e1 = __ldcs(rq + g + T);
     // pairs inside the cluster: lane g takes member g as one more entry
     if (g < ni) {
         const float4 pb = __ldg(P + fi + g);
@@ -537,7 +541,7 @@ __global__ void __launch_bounds__(CL_THREADS, M == 2 ? 6 : (M == 4 ? 5 : 4)) k_c
         cp_async_commit();
         const uint4 e = e0;
         e0 = e1;
-        if (q + 2 * T < nq) e1 = __ldg(rq + q + 2 * T);
+        if (q + 2 * T < nq) e1 = __ldcs(rq + q + 2 * T);
         cp_async_wait_1();
         const float4 p0 = s_stage[st][0][tid], p1 = s_stage[st][1][tid], p2 = s_stage[st][2][tid], p3 = s_stage[st][3][tid];
         entry(p0, (int)e.x);
@@ -549,7 +553,7 @@ __global__ void __launch_bounds__(CL_THREADS, M == 2 ? 6 : (M == 4 ? 5 : 4)) k_c
     cp_async_wait_all();
     // entries with a periodic image: the exact image arithmetic, pair by pair
     for (int e = g; e < nb; e += T) {
-        const uint32_t ent = __ldg(row + cap - 1 - e);
+        const uint32_t ent = __ldcs(row + cap - 1 - e);
         const int j = (int)(ent & JMASK);
         if (!lj_check(j < S.n, C, CHECK_CL_BACK)) break;
         int sx, sy, sz;
@@ -650,7 +654,7 @@ void cl_dispatch(const Dev<R> &S, const ljsel_config &cfg, int mode, bool ev, in
 
 template <typename R, int M, bool N3L>
 void cl_build_go(const Dev<R> &S, cudaStream_t st) {
-    const int blocks = div_up((long long)S.ncl_cap * 32, CLB_THREADS);
+    const int blocks = std::min(div_up((long long)S.ncl_cap * 32, CLB_THREADS), 152 * 16);
     if (S.reach == 1) k_cl_build<R, M, N3L, 1><<<blocks, CLB_THREADS, 0, st>>>(S);
     else k_cl_build<R, M, N3L, 2><<<blocks, CLB_THREADS, 0, st>>>(S);
 }
