@@ -57,9 +57,12 @@ typedef enum ljsel_method {
                                   particles of the cells within reach (no list)  */
     LJSEL_METHOD_VL = 1,       /* Verlet lists: per-particle lists of neighbours
                                   within r_c + skin, rebuilt every R steps        */
-    LJSEL_METHOD_CLUSTER = 2,  /* cluster-pair Verlet lists: groups of M spatially
-                                  sorted particles, lists of j-clusters per
-                                  i-cluster (M = 4, 8 or 32)                      */
+    LJSEL_METHOD_CLUSTER = 2,  /* cluster lists (the paper's Verlet list cells):
+                                  i-clusters of M = 2, 4 or 8 consecutive
+                                  sorted particles of one cell, each with one
+                                  list of the j-particles within r_c + skin of
+                                  any member; threads_per_unit lanes (M .. 32)
+                                  per i-cluster                                  */
     LJSEL_METHOD_VLW = 3       /* Verlet lists over shared-memory windows: cells are
                                   cut into strips of <= 128 particles, each CTA
                                   stages its strip's neighbourhood (<= 2047
@@ -90,7 +93,8 @@ typedef struct ljsel_params {
                                   with its velocity component reversed, the
                                   walled heating sphere of Sec. 6); 0:
                                   periodic.  Walls are available with the
-                                  LC and VL methods of single systems.        */
+                                  LC, VL and CLUSTER methods of single
+                                  systems.                                    */
     int32_t pad;
 } ljsel_params;
 
@@ -98,12 +102,12 @@ typedef struct ljsel_params {
  * traversal / N3L / cell-size-factor combination, Sec. 2.2).             */
 typedef struct ljsel_config {
     int32_t method;            /* ljsel_method                                 */
-    int32_t cluster_size;      /* CLUSTER: 4, 8 or 32; ignored otherwise       */
+    int32_t cluster_size;      /* CLUSTER: 2, 4 or 8; ignored otherwise        */
     int32_t newton3;           /* 1: each pair evaluated once and applied to
                                   both particles (Sec. 2.1); 0: twice          */
-    int32_t threads_per_unit;  /* threads sharing one particle (LC, VL: 1, 2, 4
-                                  or 8) or one i-cluster (CLUSTER: M, 2M or 4M,
-                                  at most 32 ... 128)                          */
+    int32_t threads_per_unit;  /* threads sharing one particle (VL: a power of
+                                  two <= 32; LC and VLW: 1) or one i-cluster
+                                  (CLUSTER: a power of two from M to 32)       */
     int32_t rebuild_interval;  /* R >= 1: rebuild at least every R steps; a
                                   rebuild also happens as soon as a particle
                                   has moved skin/2 since the last one          */
@@ -259,7 +263,10 @@ ljsel_status ljsel_rebuild(ljsel_system s);
  * with the current configuration (Sec. 2.1).  forces: n x 3 (host or
  * device; NULL to skip), in input order.  energy: shifted potential energy
  * sum over pairs; virial: sum over pairs of r_ij . F_ij (both host double,
- * NULL to skip).  Synchronizes the stream.                                */
+ * NULL to skip).  With energy and virial both NULL the forces come from
+ * the force arithmetic of the stepping kernels (no sums accumulated), else
+ * from the kernels that also accumulate the sums.  Synchronizes the
+ * stream.                                                                 */
 ljsel_status ljsel_compute(ljsel_system s, double *forces, int32_t on_device,
                            double *energy, double *virial);
 
@@ -580,12 +587,11 @@ ljsel_status ljsel_measure_peaks(double target_ms, ljsel_peaks *out);
  *      captured.
  *   stream: cudaStream_t or NULL.
  * The first call in a CUDA context resolves the device address of the
- * static array (with that device current) and caches it per context; make
- * that first call before any stream capture.  All calls share the array and
- * it keeps the last call's contents (each call clears what must start at
- * zero); calls whose GPU work overlaps (on different streams or from
- * different threads) race on it, so serialize them.  Calls no cudaMalloc,
- * cudaFree or other allocating routine.                                   */
+ * static array (with that device current) and caches it per context.  All
+ * calls share the array and it keeps the last call's contents (each call
+ * clears what must start at zero); calls whose GPU work overlaps (on
+ * different streams or from different threads) race on it, so serialize
+ * them.  Calls no cudaMalloc, cudaFree or other allocating routine.       */
 ljsel_status ljsel_compute_forces_noalloc(const ljsel_params *params, int64_t n, const double *pos,
                                           const int32_t *types, double *forces, double *energy, double *virial,
                                           void *stream);
