@@ -352,12 +352,17 @@ def ljsel_rebuild(h):
     _check(lib().ljsel_rebuild(h))
 
 
-def ljsel_compute(h, forces=None):
+def ljsel_compute(h, forces=None, sums=True):
+    """Forces (into `forces`) and, with sums=True, (energy, virial); with
+    sums=False only the forces, by the stepping kernels' arithmetic."""
     e = ctypes.c_double()
     w = ctypes.c_double()
     fp, dev = _ptr(forces)
-    _check(lib().ljsel_compute(h, fp, dev, ctypes.byref(e), ctypes.byref(w)))
-    return e.value, w.value
+    if sums:
+        _check(lib().ljsel_compute(h, fp, dev, ctypes.byref(e), ctypes.byref(w)))
+        return e.value, w.value
+    _check(lib().ljsel_compute(h, fp, dev, None, None))
+    return None
 
 
 def ljsel_step(h, nsteps):
@@ -659,6 +664,12 @@ class System:
         F = np.zeros((self.n, 3))
         e, w = ljsel_compute(self.h, F)
         return F, e, w
+
+    def forces(self):
+        """Forces only (n x 3), by the force arithmetic of the stepping kernels."""
+        F = np.zeros((self.n, 3))
+        ljsel_compute(self.h, F, sums=False)
+        return F
 
     def step(self, nsteps):
         ljsel_step(self.h, nsteps)

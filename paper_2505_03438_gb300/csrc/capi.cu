@@ -520,7 +520,10 @@ ljsel_status ljsel_compute(ljsel_system h, double *forces, int32_t on_device, do
     if (!s) { set_error("NULL handle"); return LJSEL_ERR_ARG; }
     return dispatch(s, [&](auto z) -> ljsel_status {
         using R = decltype(z);
-        TRY(s->compute_forces<R>(true));
+        // with neither sum wanted the stepping kernels' force path runs (no
+        // energy or virial accumulation)
+        const bool ev = energy != nullptr || virial != nullptr;
+        TRY(s->compute_forces<R>(ev));
         Dev<R> S;
         s->fill_dev(S);
         if (forces) {

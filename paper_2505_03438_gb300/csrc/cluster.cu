@@ -393,6 +393,33 @@ struct FastTab {
     unsigned band_bits; // bits(hi) - bits(lo): lo <= r^2 <= hi iff bits(r^2) - bits(lo) <= band_bits (unsigned)
 };
 
+// The pairs of one half-pair h of members with one listed particle, given
+// their displacements: returns whether r^2 of a counted pair fell in the
+// band (such a pair is left out here).  ka / kb: whether each half counts.
+template <bool N3L>
+__device__ __forceinline__ bool fast_pairs(const float2 &dx, const float2 &dy, const float2 &dz, bool ka, bool kb,
+                                           float2 &fx, float2 &fy, float2 &fz, float2 &gx, float2 &gy, float2 &gz,
+                                           const FastTab &t) {
+    float2 r2 = __fmul2_rn(dx, dx);
+    r2 = __ffma2_rn(dy, dy, r2);
+    r2 = __ffma2_rn(dz, dz, r2);
+    const bool near = (ka && __float_as_uint(r2.x) - t.lo_bits <= t.band_bits) ||
+                      (kb && __float_as_uint(r2.y) - t.lo_bits <= t.band_bits);
+    // out of range or excluded (the member itself, at distance 0): s = 0
+    const float2 sv = make_float2(ka && r2.x < t.lo ? fast_rcp(r2.x) : 0.f, kb && r2.y < t.lo ? fast_rcp(r2.y) : 0.f);
+    const float2 s2 = __fmul2_rn(sv, sv);
+    const float2 fr = __fmul2_rn(__fmul2_rn(s2, s2), __ffma2_rn(t.a2, __fmul2_rn(s2, sv), t.nb2));
+    fx = __ffma2_rn(fr, dx, fx);
+    fy = __ffma2_rn(fr, dy, fy);
+    fz = __ffma2_rn(fr, dz, fz);
+    if (N3L) {
+        gx = __ffma2_rn(fr, dx, gx);
+        gy = __ffma2_rn(fr, dy, gy);
+        gz = __ffma2_rn(fr, dz, gz);
+    }
+    return near;
+}
+
 // One listed particle j against the members: returns whether r^2 of some
 // counted pair fell in the band (those pairs are left out here).  With EXCL
 // the entry is the cluster's own member b (see cl_entry): member m's half
@@ -406,27 +433,42 @@ __device__ __forceinline__ bool fast_entry(const float4 &pj, const float2 (&mx)[
     bool near = false;
 #pragma unroll
     for (int h = 0; h < M / 2; ++h) {
-        const float2 dx = sub2(mx[h], jx), dy = sub2(my[h], jy), dz = sub2(mz[h], jz);
-        float2 r2 = __fmul2_rn(dx, dx);
-        r2 = __ffma2_rn(dy, dy, r2);
-        r2 = __ffma2_rn(dz, dz, r2);
         const bool ka = !EXCL || (N3L ? 2 * h < b : 2 * h != b);
         const bool kb = !EXCL || (N3L ? 2 * h + 1 < b : 2 * h + 1 != b);
-        near = near || (ka && __float_as_uint(r2.x) - t.lo_bits <= t.band_bits) ||
-               (kb && __float_as_uint(r2.y) - t.lo_bits <= t.band_bits);
-        // out of range or excluded (the member itself, at distance 0): s = 0
-        const float2 sv = make_float2(ka && r2.x < t.lo ? fast_rcp(r2.x) : 0.f, kb && r2.y < t.lo ? fast_rcp(r2.y) : 0.f);
-        const float2 s2 = __fmul2_rn(sv, sv);
-        const float2 fr = __fmul2_rn(__fmul2_rn(s2, s2), __ffma2_rn(t.a2, __fmul2_rn(s2, sv), t.nb2));
-        fx[h] = __ffma2_rn(fr, dx, fx[h]);
-        fy[h] = __ffma2_rn(fr, dy, fy[h]);
-        fz[h] = __ffma2_rn(fr, dz, fz[h]);
-        if (N3L) {
-            gx = __ffma2_rn(fr, dx, gx);
-            gy = __ffma2_rn(fr, dy, gy);
-            gz = __ffma2_rn(fr, dz, gz);
-        }
+        near |= fast_pairs<N3L>(sub2(mx[h], jx), sub2(my[h], jy), sub2(mz[h], jz), ka, kb, fx[h], fy[h], fz[h], gx, gy,
+                                gz, t);
     }
+    return near;
+}
+
+// image_dx on both halves: x_i - (x_j + s L) from the rounded difference,
+// its exact rounding error and the two parts of L, each operation rounded
+// as in the scalar form, so both halves equal image_dx bit for bit.
+__device__ __forceinline__ float2 image_dx2(const float2 &xi, float xj, int s, float L, float Llo) {
+    const float2 j2 = f2(xj);
+    const float2 d = sub2(xi, j2);
+    const float2 bb = sub2(d, xi);
+    const float2 lo = __fadd2_rn(sub2(xi, sub2(d, bb)), sub2(f2(-xj), bb));
+    const float sL = s > 0 ? L : -L;
+    const float sLlo = s > 0 ? Llo : -Llo;
+    const float2 r = __fadd2_rn(sub2(d, f2(sL)), sub2(lo, f2(sLlo)));
+    return s == 0 ? d : r;
+}
+
+// One listed particle j with periodic image (sx, sy, sz) against the members.
+template <int M, bool N3L>
+__device__ __forceinline__ bool fast_image_entry(const float4 &pj, int sx, int sy, int sz, const Dev<float> &S,
+                                                 const float2 (&mx)[M / 2], const float2 (&my)[M / 2],
+                                                 const float2 (&mz)[M / 2], float2 (&fx)[M / 2], float2 (&fy)[M / 2],
+                                                 float2 (&fz)[M / 2], float2 &gx, float2 &gy, float2 &gz,
+                                                 const FastTab &t) {
+    bool near = false;
+#pragma unroll
+    for (int h = 0; h < M / 2; ++h)
+        near |= fast_pairs<N3L>(image_dx2(mx[h], pj.x, sx, S.box[0], S.box_lo[0]),
+                                image_dx2(my[h], pj.y, sy, S.box[1], S.box_lo[1]),
+                                image_dx2(mz[h], pj.z, sz, S.box[2], S.box_lo[2]), true, true, fx[h], fy[h], fz[h], gx,
+                                gy, gz, t);
     return near;
 }
 
@@ -513,14 +555,37 @@ __global__ void __launch_bounds__(CL_THREADS, M == 2 ? 6 : (M == 4 ? 5 : 4)) k_c
         cp_async16(&s_stage[st][2][tid], P + e.z);
         cp_async16(&s_stage[st][3][tid], P + e.w);
     };
-    auto entry = [&](const float4 &pj, int j) {
-        float2 gx = f2(0.f), gy = f2(0.f), gz = f2(0.f);
-        const bool near = fast_entry<M, N3L>(pj, mx, my, mz, fx, fy, fz, gx, gy, gz, t);
-        float hx = gx.x + gx.y, hy = gy.x + gy.y, hz = gz.x + gz.y;
+    // one chunk of four entries: the four are evaluated before a single
+    // vote, so that their arithmetic can interleave; the band pairs of the
+    // flagged entries are then decided exactly.  With N3L each entry's
+    // -F_ij goes to F_j at once, and a band pair's with one more atomic.
+    auto chunk = [&](const float4 (&pj)[4], const uint4 &e) {
+        const unsigned js[4] = {e.x, e.y, e.z, e.w};
+        unsigned nm = 0u;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float2 gx = f2(0.f), gy = f2(0.f), gz = f2(0.f);
+            nm |= (fast_entry<M, N3L>(pj[k], mx, my, mz, fx, fy, fz, gx, gy, gz, t) ? 1u : 0u) << k;
+            if (N3L) {
+                const float hx = gx.x + gx.y, hy = gy.x + gy.y, hz = gz.x + gz.y;
+                if (js[k] < (unsigned)S.n && (hx != 0.f || hy != 0.f || hz != 0.f))
+                    atomicAdd(S.force + js[k], make_float4(-hx, -hy, -hz, 0.f));
+            }
+        }
         // the vote runs among the lanes still in the loop (groups of a warp
         // have rows of different length)
-        if (__any_sync(__activemask(), near) && near) band_entry<M, N3L>(S, pj, 0, 0, 0, mx, my, mz, fx, fy, fz, hx, hy, hz, t);
-        if (N3L && j < S.n && (hx != 0.f || hy != 0.f || hz != 0.f)) atomicAdd(S.force + j, make_float4(-hx, -hy, -hz, 0.f));
+        if (__any_sync(__activemask(), nm != 0u) && nm) {
+            while (nm) {
+                const int k = __ffs(nm) - 1;
+                nm &= nm - 1u;
+                const float4 q = k == 0 ? pj[0] : (k == 1 ? pj[1] : (k == 2 ? pj[2] : pj[3]));
+                float bx = 0.f, by = 0.f, bz = 0.f;
+                band_entry<M, N3L>(S, q, 0, 0, 0, mx, my, mz, fx, fy, fz, bx, by, bz, t);
+                const unsigned j = k == 0 ? js[0] : (k == 1 ? js[1] : (k == 2 ? js[2] : js[3]));
+                if (N3L && j < (unsigned)S.n && (bx != 0.f || by != 0.f || bz != 0.f))
+                    atomicAdd(S.force + j, make_float4(-bx, -by, -bz, 0.f));
+            }
+        }
     };
     uint4 e0 = make_uint4(0u, 0u, 0u, 0u), e1 = e0;
     if (g < nq) { e0 = __ldcs(rq + g); issue(0, e0); }
@@ -543,15 +608,13 @@ __global__ void __launch_bounds__(CL_THREADS, M == 2 ? 6 : (M == 4 ? 5 : 4)) k_c
         e0 = e1;
         if (q + 2 * T < nq) e1 = __ldcs(rq + q + 2 * T);
         cp_async_wait_1();
-        const float4 p0 = s_stage[st][0][tid], p1 = s_stage[st][1][tid], p2 = s_stage[st][2][tid], p3 = s_stage[st][3][tid];
-        entry(p0, (int)e.x);
-        entry(p1, (int)e.y);
-        entry(p2, (int)e.z);
-        entry(p3, (int)e.w);
+        const float4 pj[4] = {s_stage[st][0][tid], s_stage[st][1][tid], s_stage[st][2][tid], s_stage[st][3][tid]};
+        chunk(pj, e);
         st ^= 1;
     }
     cp_async_wait_all();
-    // entries with a periodic image: the exact image arithmetic, pair by pair
+    // entries with a periodic image: the same packed arithmetic with the
+    // image displacement of image_dx
     for (int e = g; e < nb; e += T) {
         const uint32_t ent = __ldcs(row + cap - 1 - e);
         const int j = (int)(ent & JMASK);
@@ -559,23 +622,11 @@ __global__ void __launch_bounds__(CL_THREADS, M == 2 ? 6 : (M == 4 ? 5 : 4)) k_c
         int sx, sy, sz;
         decode_image(ent >> JBITS, sx, sy, sz);
         const float4 pj = __ldg(P + j);
-        float hx = 0.f, hy = 0.f, hz = 0.f;
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-            const float4 pa = make_float4(half_of(mx[m / 2], m & 1), half_of(my[m / 2], m & 1), half_of(mz[m / 2], m & 1), 0.f);
-            const float dx = image_dx(pa.x, pj.x, sx, S.box[0], S.box_lo[0]);
-            const float dy = image_dx(pa.y, pj.y, sy, S.box[1], S.box_lo[1]);
-            const float dz = image_dx(pa.z, pj.z, sz, S.box[2], S.box_lo[2]);
-            const float r2 = r2_of(dx, dy, dz);
-            const bool in = Cut<float>::in(r2, t.lo, t.hi, pa, pj, sx, sy, sz, S.boxd, S.tab.rc2d[0]);
-            float sr6;
-            float fr = lj_fr(r2, S.tab.sig2[0], S.tab.e24[0], S.tab.e48[0], sr6);
-            fr = in ? fr : 0.f;
-            half_of(fx[m / 2], m & 1) += fr * dx;
-            half_of(fy[m / 2], m & 1) += fr * dy;
-            half_of(fz[m / 2], m & 1) += fr * dz;
-            if (N3L) { hx += fr * dx; hy += fr * dy; hz += fr * dz; }
-        }
+        float2 gx = f2(0.f), gy = f2(0.f), gz = f2(0.f);
+        const bool near = fast_image_entry<M, N3L>(pj, sx, sy, sz, S, mx, my, mz, fx, fy, fz, gx, gy, gz, t);
+        float hx = gx.x + gx.y, hy = gy.x + gy.y, hz = gz.x + gz.y;
+        if (__any_sync(__activemask(), near) && near)
+            band_entry<M, N3L>(S, pj, sx, sy, sz, mx, my, mz, fx, fy, fz, hx, hy, hz, t);
         if (N3L && (hx != 0.f || hy != 0.f || hz != 0.f)) atomicAdd(S.force + j, make_float4(-hx, -hy, -hz, 0.f));
     }
     float ax[M], ay[M], az[M];
