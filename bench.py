@@ -268,15 +268,19 @@ def batch_leg(peaks, steps=500, warmup=5, trial_steps=10, profile_steps=30, eage
     return out
 
 
-def inhomogeneous_leg(steps=20000, every=1000, strategy="predictive", fixed_steps=None, skip_within=0.05):
+def inhomogeneous_leg(steps=20000, every=1000, strategies=("predictive", "expert"), fixed_steps=None,
+                      skip_within=0.05, repeats=3):
     """Heated liquid ball (radius 40, density 0.8, T 3.0) in vapour (density
     0.01, T 1.2), periodic box 200, about 292k particles: `steps` steps with
     a tuning phase every `every` steps (trial steps count as steps; a phase
     whose live statistics moved less than skip_within since the last phase
-    with trials is skipped), once with `strategy` and once with the Random
-    Forest strategy (the shipped forest, one configuration trialled a phase),
-    against every fixed configuration run over the same steps from the same
-    state."""
+    with trials is skipped), once with each of `strategies` and `repeats`
+    times with the Random Forest strategy (the shipped forest), against the
+    fixed configurations run over the same steps from the same state: every
+    candidate screened over the first 1000 steps, the best five over all
+    steps, the best two of those again so that each has `repeats` runs; the
+    forest's runs and the fixed re-runs alternate, and the comparison is
+    between medians."""
     import torch
 
     import paper_2505_03438_gb300 as lj
@@ -295,7 +299,8 @@ def inhomogeneous_leg(steps=20000, every=1000, strategy="predictive", fixed_step
         torch.cuda.synchronize()
         return a.elapsed_time(b)
 
-    def tuned_run(strat, phases):
+    def tuned_run(strat):
+        phases = []
         s = lj.System(sc, stream=stream.cuda_stream)
         s.step(3)
         if strat == "forest":
@@ -312,13 +317,11 @@ def inhomogeneous_leg(steps=20000, every=1000, strategy="predictive", fixed_step
 
         ms = timed(run)
         s.close()
-        return ms
+        return {"value": n * steps / (ms * 1e-3), "strategy": strat,
+                "phases_skipped": sum(p["skipped"] for p in phases),
+                "tuning_overhead_ms": sum(p["overhead_ms"] for p in phases),
+                "tuning_phase_ms": sum(p["phase_ms"] for p in phases), "phases": phases}
 
-    phases, phases_rf = [], []
-    ms = tuned_run(strategy, phases)
-    ms_rf = tuned_run("forest", phases_rf)
-    # fixed configurations: every candidate screened over the first
-    # `screen` steps, the best five run over all `steps` from the same state
     probe = lj.System(sc)
     cands = lj.ljsel_default_candidates(probe.h)
     probe.close()
@@ -334,26 +337,34 @@ def inhomogeneous_leg(steps=20000, every=1000, strategy="predictive", fixed_step
         finally:
             f.close()
 
+    others = {st: tuned_run(st) for st in strategies}
+    forest_runs = [tuned_run("forest")]
     screen = min(steps, 1000 if fixed_steps is None else fixed_steps)
     screened = {c.name(): (c, run_fixed(c, screen)) for c in cands}
     screened = {k: v for k, v in screened.items() if v[1] is not None}
     top = sorted(screened.values(), key=lambda cv: -cv[1])[:5]
-    fixed = {c.name(): run_fixed(c, steps) for c, _ in top}
-    fixed = {k: v for k, v in fixed.items() if v is not None}
-    best = max(fixed.items(), key=lambda kv: kv[1]) if fixed else None
-    return {"workload": "heated_sphere: N=%d, box 200, ball r 40 rho 0.8 T 3.0, vapour rho 0.01 T 1.2, rc 2.5, "
-                        "skin 0.3" % n,
-            "value": n * steps / (ms * 1e-3), "unit": UNIT, "steps": steps, "retune_every": every,
-            "strategy": strategy, "skip_within": skip_within,
-            "phases_skipped": sum(p["skipped"] for p in phases),
-            "tuning_overhead_ms": sum(p["overhead_ms"] for p in phases),
-            "tuning_phase_ms": sum(p["phase_ms"] for p in phases), "phases": phases,
-            "forest": {"value": n * steps / (ms_rf * 1e-3), "strategy": "forest", "forest_top": 1,
-                       "phases_skipped": sum(p["skipped"] for p in phases_rf),
-                       "tuning_overhead_ms": sum(p["overhead_ms"] for p in phases_rf),
-                       "tuning_phase_ms": sum(p["phase_ms"] for p in phases_rf), "phases": phases_rf},
-            "fixed_screen_steps": screen, "fixed_screened": {k: v[1] for k, v in screened.items()},
-            "fixed": fixed, "best_fixed": best}
+    fixed = {c.name(): [run_fixed(c, steps)] for c, _ in top}
+    fixed = {k: v for k, v in fixed.items() if v[0] is not None}
+    byname = {c.name(): c for c, _ in top}
+    best2 = sorted(fixed, key=lambda k: -fixed[k][0])[:2]
+    for _ in range(repeats - 1):
+        forest_runs.append(tuned_run("forest"))
+        for k in best2:
+            fixed[k].append(run_fixed(byname[k], steps))
+    med = {k: statistics.median(v) for k, v in fixed.items() if len(v) == repeats}
+    best = max(med.items(), key=lambda kv: kv[1]) if med else None
+    forest_med = statistics.median(r["value"] for r in forest_runs)
+    fr = dict(forest_runs[0], forest_top=1, values=[r["value"] for r in forest_runs], median=forest_med)
+    out = {"workload": "heated_sphere: N=%d, box 200, ball r 40 rho 0.8 T 3.0, vapour rho 0.01 T 1.2, rc 2.5, "
+                       "skin 0.3" % n,
+           "unit": UNIT, "steps": steps, "retune_every": every, "skip_within": skip_within, "repeats": repeats,
+           "forest": fr, "fixed_screen_steps": screen, "fixed_screened": {k: v[1] for k, v in screened.items()},
+           "fixed": fixed, "best_fixed": best,
+           "tuned_over_best_fixed": {"forest": forest_med / best[1] if best else None}}
+    for st, r in others.items():
+        out[st] = r
+        out["tuned_over_best_fixed"][st] = r["value"] / best[1] if best else None
+    return out
 
 
 def walled_leg(steps=150000, every=1000, thermo_every=100, d_t=0.1, target=100.0, strategies=("forest", "predictive")):

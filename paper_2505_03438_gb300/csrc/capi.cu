@@ -186,6 +186,9 @@ std::vector<ljsel_config> default_candidates(const System &s) {
     for (int t : {2, 4, 8}) add(LJSEL_METHOD_CLUSTER, 2, 0, t, 1.0, R);
     for (int t : {4, 8, 16}) add(LJSEL_METHOD_CLUSTER, 4, 0, t, 1.0, R);
     for (int t : {8, 16}) add(LJSEL_METHOD_CLUSTER, 8, 0, t, 1.0, R);
+    // with the list rebuilt every 2R steps where displacements allow it
+    add(LJSEL_METHOD_CLUSTER, 2, 0, 4, 1.0, 2 * R);
+    for (int t : {8, 16}) add(LJSEL_METHOD_CLUSTER, 4, 0, t, 1.0, 2 * R);
     add(LJSEL_METHOD_CLUSTER, 2, 1, 4, 1.0, R);
     add(LJSEL_METHOD_CLUSTER, 4, 1, 8, 1.0, R);
     add(LJSEL_METHOD_CLUSTER, 8, 1, 8, 1.0, R);

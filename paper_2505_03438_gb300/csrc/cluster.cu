@@ -499,10 +499,11 @@ __device__ __forceinline__ void band_entry(const Dev<float> &S, const float4 &pj
     }
 }
 
-// Register bound by cluster size: 80 for M = 2 (24 warps per SM), 102 for
-// M = 4, 128 for M = 8.
+// Register bound by cluster size (measured on the 1M liquid): M = 2, 80
+// registers (24 warps per SM) without N3L, 64 (32 warps) with N3L; M = 4, 80
+// (24 warps); M = 8, 128 (16 warps).
 template <int M, bool N3L, int MODE>
-__global__ void __launch_bounds__(CL_THREADS, M == 2 ? 6 : (M == 4 ? 5 : 4)) k_cl_fast(Dev<float> S, int T) {
+__global__ void __launch_bounds__(CL_THREADS, M == 2 ? (N3L ? 8 : 6) : (M == 4 ? 6 : 4)) k_cl_fast(Dev<float> S, int T) {
     Ctrl *C = S.ctrl;
     if (C->overflow) return;
     const int gid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -555,6 +556,7 @@ __global__ void __launch_bounds__(CL_THREADS, M == 2 ? 6 : (M == 4 ? 5 : 4)) k_c
         cp_async16(&s_stage[st][2][tid], P + e.z);
         cp_async16(&s_stage[st][3][tid], P + e.w);
     };
+    int st = 0;
     // one chunk of four entries: the four are evaluated before a single
     // vote, so that their arithmetic can interleave; the band pairs of the
     // flagged entries are then decided exactly.  With N3L each entry's
@@ -578,7 +580,7 @@ __global__ void __launch_bounds__(CL_THREADS, M == 2 ? 6 : (M == 4 ? 5 : 4)) k_c
             while (nm) {
                 const int k = __ffs(nm) - 1;
                 nm &= nm - 1u;
-                const float4 q = k == 0 ? pj[0] : (k == 1 ? pj[1] : (k == 2 ? pj[2] : pj[3]));
+                const float4 q = s_stage[st][k][tid];  // reloaded: pj need not stay in registers
                 float bx = 0.f, by = 0.f, bz = 0.f;
                 band_entry<M, N3L>(S, q, 0, 0, 0, mx, my, mz, fx, fy, fz, bx, by, bz, t);
                 const unsigned j = k == 0 ? js[0] : (k == 1 ? js[1] : (k == 2 ? js[2] : js[3]));
@@ -600,7 +602,6 @@ __global__ void __launch_bounds__(CL_THREADS, M == 2 ? 6 : (M == 4 ? 5 : 4)) k_c
         if (near) band_entry<M, N3L, true>(S, pb, 0, 0, 0, mx, my, mz, fx, fy, fz, hx, hy, hz, t, g);
         if (N3L && (hx != 0.f || hy != 0.f || hz != 0.f)) atomicAdd(S.force + fi + g, make_float4(-hx, -hy, -hz, 0.f));
     }
-    int st = 0;
     for (int q = g; q < nq; q += T) {
         if (q + T < nq) issue(st ^ 1, e1);
         cp_async_commit();

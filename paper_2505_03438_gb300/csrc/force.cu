@@ -296,9 +296,9 @@ __global__ void __launch_bounds__(256) k_integrate(Dev<R> S) {
     bool exceeded = false, bad = false;
     if (i < S.n) {
         const int sp = C->state_par, pp = C->pos_par;
-        V4<R> f = S.force[i];
-        S.force[i] = make_pos((R)0, (R)0, (R)0, 0);
+        const V4<R> f = S.force[i];
         integrate_one<R, EV>(S, sp, pp, C->half_kick, i, S.type[sp][i], f.x, f.y, f.z, ke, exceeded, bad);
+        S.force[i] = make_pos((R)0, (R)0, (R)0, 0);  // after the loads of the update
     }
     report_flags(C, exceeded, bad);
     if (EV) block_sum3(0.0, 0.0, ke, C);

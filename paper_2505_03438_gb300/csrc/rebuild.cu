@@ -22,7 +22,7 @@ constexpr unsigned long long FLAG_P = 2ull << 62;  // inclusive prefix published
 constexpr unsigned long long VAL_MASK = (1ull << 62) - 1ull;
 constexpr int SPIN_LIMIT = 1 << 22;
 constexpr int VL_BUILD_THREADS = 128;
-constexpr int VL_BUILD_MIN_BLOCKS = 10;  // 40 warps per SM: at most 48 registers a thread, no spills
+constexpr int VL_BUILD_MIN_BLOCKS = 8;  // 32 warps per SM: at most 64 registers a thread
 
 __device__ __forceinline__ unsigned morton3(unsigned x, unsigned y, unsigned z) {
     unsigned k = 0;
@@ -240,7 +240,8 @@ __global__ void k_sortgather(Dev<R> S) {
 // half stencil.  The stencil is walked as (y, z) rows of cells; in each row
 // the x cells cx - RCH .. cx + RCH form one run of consecutive sorted
 // particles, split only at a periodic x edge.  Candidates are tested four at
-// a time into a 32-bit mask per block of 32; only the set bits are appended.
+// a time into a 32-bit mask per block of 32 (in FP32 the sign bits of
+// r^2 - r_list^2 are funnel-shifted in); only the set bits are appended.
 // The 32 lanes of a warp are 32 consecutive sorted particles and share most
 // of their runs (cutting each particle's runs to the reach of the list
 // radius tests far fewer candidates but makes the lanes' trip counts differ,
@@ -312,19 +313,31 @@ __global__ void __launch_bounds__(VL_BUILD_THREADS, VL_BUILD_MIN_BLOCKS) k_vl_bu
                 for (int j0 = jb; j0 < je; j0 += 32) {
                     const int m = min(32, je - j0);
                     uint32_t mask = 0;
-                    int t = 0;
-                    for (; t + 4 <= m; t += 4) {
-                        const int j = j0 + t;
-                        const V4<R> q0 = ldpos(P, j), q1 = ldpos(P, j + 1), q2 = ldpos(P, j + 2), q3 = ldpos(P, j + 3);
-                        const uint32_t bits = (uint32_t)(r2_of(xs - q0.x, ys - q0.y, zs - q0.z) < S.rlist2) |
-                                              ((uint32_t)(r2_of(xs - q1.x, ys - q1.y, zs - q1.z) < S.rlist2) << 1) |
-                                              ((uint32_t)(r2_of(xs - q2.x, ys - q2.y, zs - q2.z) < S.rlist2) << 2) |
-                                              ((uint32_t)(r2_of(xs - q3.x, ys - q3.y, zs - q3.z) < S.rlist2) << 3);
-                        mask |= bits << t;
-                    }
-                    for (; t < m; ++t) {
-                        const V4<R> q = ldpos(P, j0 + t);
-                        mask |= (uint32_t)(r2_of(xs - q.x, ys - q.y, zs - q.z) < S.rlist2) << t;
+                    if constexpr (sizeof(R) == 4) {
+                        // the sign bit of r^2 - r_list^2 (set when the
+                        // candidate is inside) is shifted into the mask:
+                        // candidate t lands at bit m - 1 - t, reversed below
+                        const float nrl2 = -(float)S.rlist2;
+                        auto below = [&](const V4<R> &q) {
+                            const float ex = xs - q.x, ey = ys - q.y, ez = zs - q.z;
+                            return __float_as_uint(fmaf(ez, ez, fmaf(ey, ey, fmaf(ex, ex, nrl2))));
+                        };
+                        int t = 0;
+                        for (; t + 4 <= m; t += 4) {
+                            const int j = j0 + t;
+                            const V4<R> q0 = ldpos(P, j), q1 = ldpos(P, j + 1), q2 = ldpos(P, j + 2), q3 = ldpos(P, j + 3);
+                            mask = __funnelshift_l(below(q0), mask, 1);
+                            mask = __funnelshift_l(below(q1), mask, 1);
+                            mask = __funnelshift_l(below(q2), mask, 1);
+                            mask = __funnelshift_l(below(q3), mask, 1);
+                        }
+                        for (; t < m; ++t) mask = __funnelshift_l(below(ldpos(P, j0 + t)), mask, 1);
+                        mask = __brev(mask) >> (32 - m);
+                    } else {
+                        for (int t = 0; t < m; ++t) {
+                            const V4<R> q = ldpos(P, j0 + t);
+                            mask |= (uint32_t)(r2_of(xs - q.x, ys - q.y, zs - q.z) < S.rlist2) << t;
+                        }
                     }
                     if (self) {  // drop j == i
                         const int rel = ii - j0;

@@ -37,9 +37,13 @@ __device__ __forceinline__ void integrate_one(const Dev<R> &S, int sp, int pp, i
     const int n = S.n;
     double *X = S.x[sp];
     double *V = S.v[sp];
+    // every load first, so that they are in flight together (the stores
+    // below may alias them as far as the compiler knows)
+    double vx = V[i], vy = V[n + i], vz = V[2 * n + i];
+    const double x0 = X[i], y0 = X[n + i], z0 = X[2 * n + i];
+    const V4<R> r = S.xref[i];
     R c = S.tab.inv_mass_dt[t];
     if (half) c *= (R)0.5;
-    double vx = V[i], vy = V[n + i], vz = V[2 * n + i];
     double dvx = (double)(c * fx), dvy = (double)(c * fy), dvz = (double)(c * fz);
     if (EV) {
         double h = half ? 0.0 : 0.5;
@@ -50,9 +54,9 @@ __device__ __forceinline__ void integrate_one(const Dev<R> &S, int sp, int pp, i
     }
     vx += dvx; vy += dvy; vz += dvz;
     const double dt = S.tab.dt;
-    double x = fma(dt, vx, X[i]);
-    double y = fma(dt, vy, X[n + i]);
-    double z = fma(dt, vz, X[2 * n + i]);
+    double x = fma(dt, vx, x0);
+    double y = fma(dt, vy, y0);
+    double z = fma(dt, vz, z0);
     // reflective walls: mirror a crossing back and reverse the velocity component
     if (S.walls[0]) { if (x < 0.0) { x = -x; vx = -vx; } else if (x > S.boxd[0]) { x = 2.0 * S.boxd[0] - x; vx = -vx; } }
     if (S.walls[1]) { if (y < 0.0) { y = -y; vy = -vy; } else if (y > S.boxd[1]) { y = 2.0 * S.boxd[1] - y; vy = -vy; } }
@@ -61,7 +65,6 @@ __device__ __forceinline__ void integrate_one(const Dev<R> &S, int sp, int pp, i
     X[i] = x; X[n + i] = y; X[2 * n + i] = z;
     V4<R> w = make_pos((R)x, (R)y, (R)z, t);
     S.pos[pp ^ 1][i] = w;
-    V4<R> r = S.xref[i];
     R ddx = w.x - r.x, ddy = w.y - r.y, ddz = w.z - r.z;
     R d2 = ddx * ddx + ddy * ddy + ddz * ddz;
     exceeded = exceeded || !(d2 < S.half_skin2);

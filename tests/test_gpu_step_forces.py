@@ -97,6 +97,7 @@ def _one_step_check(s, sc, x0, v0, p):
     m = np.asarray(sc["mass"], np.float64)[np.zeros(len(x0), np.int64) if sc.get("types") is None
                                             else np.asarray(sc["types"], np.int64)][:, None]
     s.set_state(x0, v0)
+    s.forces()  # the rebuild that set_state requested wraps the positions: read them after it
     w0 = s.work_positions()
     s.step(1)
     w1 = s.work_positions()
