@@ -856,11 +856,11 @@ ljsel_status ljsel_default_candidates(ljsel_system h, int32_t cap, ljsel_config 
 // configuration family Good / Okay / Bad; the crisp suitability is the
 // centre of gravity of the aggregated output set (Sec. 2.3), and only
 // configurations rated at least 0.5 are trialled.  The paper's rule file is
-// not available; these rules are ours, written from full searches of this
-// library: in a dense liquid (about 18 particles per bin) Verlet lists with
-// or without N3L are fastest, linked cells about 2x and the window and
-// cluster lists 1.5-3x slower; in a dilute gas the neighbour counts vanish
-// and linked cells, which build no list, are expected to win.
+// not available; these rules are ours, written from the full searches of
+// the 42 Random Forest training scenarios on this GPU: a Verlet-list
+// variant is fastest or within 18 % in every one; cluster lists win or come
+// within 1-14 % from about 4 particles per bin up and lose by 10-40 % below;
+// window lists (1.2x and more) and linked cells (1.3x and more) never win.
 struct Trap {
     double a, b, c, d;  // 0 below a, rising to 1 at b, 1 until c, 0 from d
     double operator()(double x) const {
@@ -876,7 +876,7 @@ static const Trap OUT_BAD = {-INF, -INF, 0.1, 0.4}, OUT_OKAY = {0.2, 0.5, 0.5, 0
 
 // consequent term per (family, input term): 0 bad, 1 okay, 2 good
 static int expert_rule(const ljsel_config &c, int input_term) {
-    static const int VL_[3] = {1, 2, 2}, VLW_[3] = {0, 1, 1}, LC_[3] = {2, 1, 0}, CL_[3] = {1, 0, 0};
+    static const int VL_[3] = {2, 2, 2}, VLW_[3] = {0, 0, 0}, LC_[3] = {0, 0, 0}, CL_[3] = {0, 1, 1};
     switch (c.method) {
         case LJSEL_METHOD_VL: return VL_[input_term];
         case LJSEL_METHOD_VLW: return VLW_[input_term];
@@ -986,7 +986,8 @@ ljsel_status ljsel_autotune(ljsel_system h, const ljsel_tuner_opts *opts, ljsel_
         expert_x = st.mean;
         int any = 0;
         for (size_t k = 0; k < cands.size(); ++k) {
-            trial[k] = !ent[k]->blacklisted && expert_suitability(cands[k], st.mean) >= 0.5;
+            // suitability >= 0.5 (an "okay" alone has centroid 0.5 up to rounding)
+            trial[k] = !ent[k]->blacklisted && expert_suitability(cands[k], st.mean) >= 0.5 - 1e-9;
             any += trial[k];
         }
         if (!any)

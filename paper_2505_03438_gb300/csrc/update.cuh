@@ -26,11 +26,41 @@ __device__ __forceinline__ void block_sum3(double a, double b, double c, Ctrl *C
     }
 }
 
+// FP32 <-> FP64 conversions on the integer pipes (the FP64 pipe of this part
+// runs about two operations a clock per SM, the integer pipes 64): exact for
+// zero and normal values, double to float rounded to nearest even; results
+// in the FP32 subnormal range flush to zero, and non-finite inputs are not
+// preserved (the update checks the FP32 forces for them separately, and
+// positions and velocities of a running simulation are finite and normal or
+// zero).
+__device__ __forceinline__ double f32_to_f64(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    // rebias the exponent (1023 - 127 = 896) and move the 23 mantissa bits
+    // to the top of the 52
+    const unsigned hi = (u & 0x80000000u) | (e ? (((e + 896u) << 20) | ((u & 0x7fffffu) >> 3)) : 0u);
+    const unsigned lo = e ? (u << 29) : 0u;
+    return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ float f64_to_f32(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 896;
+    // the top 23 of the 52 mantissa bits, the round bit and the sticky bits
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rb = (lo >> 28) & 1u, st = (lo & 0x0fffffffu) != 0u ? 1u : 0u;
+    // exponent and mantissa as one field, so that a rounding carry moves
+    // into the exponent (and at the top into the infinity pattern)
+    unsigned r = ((unsigned)e << 23) + m;
+    r += rb & (st | (m & 1u));
+    r = e <= 0 ? 0u : (e >= 255 ? 0x7f800000u : r);
+    return __uint_as_float((hi & 0x80000000u) | r);
+}
+
 // Stormer-Verlet update of one particle (Sec. 2.1) in leapfrog form: the
 // stored velocity is at the half step (or, with `half`, at the integer step,
 // and the kick is dt/2).  v += (dt/m) F; x += dt v; the working copy is the
-// FP32 rounding of the FP64 position.  Returns |x - x_ref|^2 exceedance and
-// the kinetic energy at the integer step (EV).
+// FP32 rounding (to nearest even) of the FP64 position.  Returns |x -
+// x_ref|^2 exceedance and the kinetic energy at the integer step (EV).
 template <typename R, bool EV>
 __device__ __forceinline__ void integrate_one(const Dev<R> &S, int sp, int pp, int half, int i, int t, R fx, R fy,
                                               R fz, double &ke, bool &exceeded, bool &bad) {
@@ -44,7 +74,12 @@ __device__ __forceinline__ void integrate_one(const Dev<R> &S, int sp, int pp, i
     const V4<R> r = S.xref[i];
     R c = S.tab.inv_mass_dt[t];
     if (half) c *= (R)0.5;
-    double dvx = (double)(c * fx), dvy = (double)(c * fy), dvz = (double)(c * fz);
+    double dvx, dvy, dvz;
+    if constexpr (sizeof(R) == 4) {
+        dvx = f32_to_f64(c * fx); dvy = f32_to_f64(c * fy); dvz = f32_to_f64(c * fz);
+    } else {
+        dvx = c * fx; dvy = c * fy; dvz = c * fz;
+    }
     if (EV) {
         double h = half ? 0.0 : 0.5;
         double ux = vx + h * (double)(S.tab.inv_mass_dt[t] * fx);
@@ -63,7 +98,9 @@ __device__ __forceinline__ void integrate_one(const Dev<R> &S, int sp, int pp, i
     if (S.walls[2]) { if (z < 0.0) { z = -z; vz = -vz; } else if (z > S.boxd[2]) { z = 2.0 * S.boxd[2] - z; vz = -vz; } }
     V[i] = vx; V[n + i] = vy; V[2 * n + i] = vz;
     X[i] = x; X[n + i] = y; X[2 * n + i] = z;
-    V4<R> w = make_pos((R)x, (R)y, (R)z, t);
+    V4<R> w;
+    if constexpr (sizeof(R) == 4) w = make_pos(f64_to_f32(x), f64_to_f32(y), f64_to_f32(z), t);
+    else w = make_pos(x, y, z, t);
     S.pos[pp ^ 1][i] = w;
     R ddx = w.x - r.x, ddy = w.y - r.y, ddz = w.z - r.z;
     R d2 = ddx * ddx + ddy * ddy + ddz * ddz;

@@ -153,3 +153,28 @@ def test_every_candidate_liquid_1m_stepping(lj):
         assert s.counters()["rebuilds"] == nreb, c.name()
         _one_step_check(s, sc, x1, sc["v"], p)
     s.close()
+
+
+@pytest.mark.parametrize("cfg", [dict(method="VL", threads_per_unit=2), dict(method="VL", newton3=True, threads_per_unit=4),
+                                 dict(method="CL", cluster_size=4, threads_per_unit=4)], ids=["VL", "VL-N3L", "CL4"])
+def test_working_positions_are_the_fp32_rounding(lj, cfg):
+    """After steps the working positions (written by the update) are the
+    FP32 round-to-nearest-even of the FP64 positions, bit for bit."""
+    sc = scenarios.liquid_1m()
+    s = lj.System(sc)
+    s.set_config(rebuild_interval=10, **cfg)
+    s.step(7)
+    w = s.work_positions()
+    x, _ = s.state()  # wrapped into [0, L); the working copy is unwrapped since the last rebuild
+    L = np.broadcast_to(np.asarray(sc["box"], np.float64), (3,))
+    same = np.asarray(x, np.float32).astype(np.float64) == w
+    for k in (-1.0, 1.0):
+        same |= np.asarray(x + k * L, np.float32).astype(np.float64) == w
+    # a coordinate that crossed a face since the last rebuild is exported
+    # wrapped, x - L rounded in FP64; within 1e-5 of the face that rounding
+    # (up to 1.4e-14) is no longer below the FP32 resolution of x, so the
+    # unwrapped value cannot be recovered bit for bit there
+    near_face = np.minimum(x, L - x) < 1e-5
+    assert (same | near_face).all(), np.argwhere(~(same | near_face))[:5]
+    assert (~same).sum() <= 10
+    s.close()
