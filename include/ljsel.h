@@ -197,6 +197,12 @@ typedef struct ljsel_tuner_report {
     int32_t skipped;           /* 1: the phase was skipped (skip_within)      */
     double expert_input;       /* expert: mean particles per CSF-1 bin; random
                                   forest: probability of its first choice     */
+    double rebuild_every;      /* the interval the build time was weighted by
+                                  for configs with a longer R: the mean steps
+                                  per rebuild observed since the last phase
+                                  when most of those rebuilds came early (a
+                                  particle reached skin/2), else 0 (each
+                                  config's own R)                             */
 } ljsel_tuner_report;
 
 /* GPU time per kernel class, measured with CUDA events around each launch
@@ -316,7 +322,9 @@ ljsel_status ljsel_get_counters(ljsel_system s, ljsel_counters *c);
  * configurations, each building its own neighbour structure and then
  * advancing opts->trial_steps steps of the simulation, keep the one with
  * the lowest cost per step (build time over R plus force and integration
- * time per step), and select it.  chosen and
+ * time per step; when most rebuilds since the last phase came early, the
+ * build time is divided by min(R, the observed steps per rebuild) instead,
+ * reported as report->rebuild_every), and select it.  chosen and
  * report may be NULL.  State (blacklist, history for the predictive
  * strategy) persists across phases of the same handle.                    */
 ljsel_status ljsel_autotune(ljsel_system s, const ljsel_tuner_opts *opts,

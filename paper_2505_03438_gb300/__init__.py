@@ -143,6 +143,7 @@ class ljsel_tuner_report(ctypes.Structure):
         ("nprobed_out", ctypes.c_int32),
         ("skipped", ctypes.c_int32),
         ("expert_input", ctypes.c_double),
+        ("rebuild_every", ctypes.c_double),
     ]
 
 

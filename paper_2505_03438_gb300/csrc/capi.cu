@@ -909,8 +909,10 @@ ljsel_status ljsel_expert_suitability(const ljsel_config *c, double mean_per_bin
 // One tuning phase.  Candidates are trialled in the order of their last
 // measured cost.  Each trial selects the configuration, builds its
 // neighbour structure (timed), then advances opts->trial_steps steps
-// (timed); cost per step = build time / R + step time / trial_steps, the
-// weighted average of build and force time of Sec. 2.2.5.  Trials advance the
+// (timed); cost per step = build time / R' + step time / trial_steps, the
+// weighted average of build and force time of Sec. 2.2.5, with R' = R, or
+// min(R, the interval observed since the last phase) when displacements
+// forced most of its rebuilds (see i_obs below).  Trials advance the
 // simulation (Sec. 1).  With probe_steps > 0 a trial whose first probe_steps
 // steps already cost more than probe_factor x the best cost of the phase
 // stops there.  Predictive strategy (Sec. 5.1): after two phases a config is
@@ -956,6 +958,27 @@ ljsel_status ljsel_autotune(ljsel_system h, const ljsel_tuner_opts *opts, ljsel_
             return LJSEL_OK;
         }
     }
+    // the rebuild interval the displacements allowed since the last phase
+    // (Sec. 2.2.1): when most rebuilds of that window came early (a particle
+    // reached skin/2 before R steps), a config's longer R would not space
+    // its builds further apart, so the build time of Sec. 2.2.5's weighted
+    // cost is divided by min(R, observed interval) instead of R
+    TRY(s->read_ctrl());
+    double i_obs = 0.0;
+    {
+        const long long ds = s->h_ctrl->total_steps - s->tune_steps0, dr = s->h_ctrl->rebuilds - s->tune_rebuilds0,
+                        de = s->h_ctrl->early_rebuilds - s->tune_early0;
+        if (ds >= 20 && dr > 0 && 2 * de >= dr) i_obs = (double)ds / (double)dr;
+    }
+    auto weight = [&](int R) { return i_obs > 0.0 ? std::min((double)R, i_obs) : (double)R; };
+    // the next window starts when this phase ends
+    auto end_window = [&]() -> ljsel_status {
+        TRY(s->read_ctrl());
+        s->tune_steps0 = s->h_ctrl->total_steps;
+        s->tune_rebuilds0 = s->h_ctrl->rebuilds;
+        s->tune_early0 = s->h_ctrl->early_rebuilds;
+        return LJSEL_OK;
+    };
     std::vector<ljsel_config> cands;
     if (opts->strategy == 3) {
         cands = s->forest.classes;  // the forest ranks its own classes
@@ -1030,6 +1053,8 @@ ljsel_status ljsel_autotune(ljsel_system h, const ljsel_tuner_opts *opts, ljsel_
             const auto &hs = ent[k]->history;
             r.chosen_cost_ms = hs.empty() ? 0.0 : hs.back().second;
             r.expert_input = expert_x;
+            r.rebuild_every = i_obs;
+            TRY(end_window());
             r.phase_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
             s->tuned_stats = st_now;
             s->have_tuned_stats = true;
@@ -1102,7 +1127,7 @@ ljsel_status ljsel_autotune(ljsel_system h, const ljsel_tuner_opts *opts, ljsel_
             tb = std::max(0.f, tb - te);
             // trials use plain stream launches: instantiating a step graph
             // per candidate would cost more than the trial itself
-            const int R_ = std::max(1, cands[k].rebuild_interval);
+            const double R_ = weight(std::max(1, cands[k].rebuild_interval));
             int probe = opts->probe_steps > 0 ? std::min(opts->probe_steps, opts->trial_steps) : opts->trial_steps;
             CK(cudaEventRecord(s->ev_a, s->stream));
             TRY(s->advance<R>(probe, true));
@@ -1148,6 +1173,7 @@ ljsel_status ljsel_autotune(ljsel_system h, const ljsel_tuner_opts *opts, ljsel_
     }
     for (auto *e : ent) nbl += e->blacklisted;
     TRY(ljsel_set_config(h, &cands[best_k]));
+    TRY(end_window());
     s->tuner_phase += 1;
     if (need_stats) {
         s->tuned_stats = st_now;
@@ -1165,6 +1191,7 @@ ljsel_status ljsel_autotune(ljsel_system h, const ljsel_tuner_opts *opts, ljsel_
     r.trial_steps_total = steps_total;
     r.nprobed_out = npo;
     r.expert_input = expert_x;
+    r.rebuild_every = i_obs;
     s->last_report = r;
     if (chosen) *chosen = cands[best_k];
     if (report) *report = r;

@@ -98,6 +98,9 @@ struct System {
     // tuner state
     std::vector<TunerEntry> tuner;
     int tuner_phase = 0;
+    // counters at the end of the last tuning phase: the window over which the
+    // next phase observes the rebuild interval
+    long long tune_steps0 = 0, tune_rebuilds0 = 0, tune_early0 = 0;
     Forest forest;  // Random Forest strategy (empty until ljsel_set_forest)
     ljsel_tuner_report last_report{};
     bool have_tuned_stats = false;

@@ -1,9 +1,11 @@
 """Training data of the Random Forest strategy (Sec. 5.3), measured on the
 GPU the library runs on: for every synthetic scenario of
-`scenarios.training_scenarios`, the live statistics (Sec. 4) at the start and
-the cost per step of every default candidate configuration, from one
-full-search tuning phase (each trial rebuilds and advances `trial_steps`
-steps, the paper's trials being ten iterations with one build).
+`scenarios.training_scenarios`, after 60 steps (so that the tuning phase
+weights the build times by the rebuild interval the displacements allow),
+the live statistics (Sec. 4) and the cost per step of every default
+candidate configuration from one full-search tuning phase (each trial
+rebuilds and advances `trial_steps` steps, the paper's trials being ten
+iterations with one build).
 
     python -m paper_2505_03438_gb300.forest_data OUT.jsonl
 """
@@ -23,7 +25,9 @@ def collect(out_path=DEFAULT_DATA, trial_steps=10, seed=7, log=print):
         for sc in scenarios.training_scenarios(seed):
             s = lj.System(sc)
             try:
-                s.step(2)
+                # enough steps for the tuning phase to observe how often the
+                # displacements force a rebuild
+                s.step(60)
                 st = s.stats()
                 s.autotune(strategy="full", trial_steps=trial_steps)
                 costs = {name: cost for name, (cost, _) in lj.ljsel_tuner_costs(s.h).items()}
