@@ -275,7 +275,8 @@ def inhomogeneous_leg(steps=20000, every=1000, strategies=("predictive", "expert
     a tuning phase every `every` steps (trial steps count as steps; a phase
     whose live statistics moved less than skip_within since the last phase
     with trials is skipped), once with each of `strategies` and `repeats`
-    times with the Random Forest strategy (the shipped forest), against the
+    times with the Random Forest strategy (the shipped forest; once more
+    trialling its three most probable classes each phase), against the
     fixed configurations run over the same steps from the same state: every
     candidate screened over the first 1000 steps, the best five over all
     steps, the best two of those again so that each has `repeats` runs; the
@@ -299,7 +300,7 @@ def inhomogeneous_leg(steps=20000, every=1000, strategies=("predictive", "expert
         torch.cuda.synchronize()
         return a.elapsed_time(b)
 
-    def tuned_run(strat):
+    def tuned_run(strat, top=1):
         phases = []
         s = lj.System(sc, stream=stream.cuda_stream)
         s.step(3)
@@ -309,7 +310,7 @@ def inhomogeneous_leg(steps=20000, every=1000, strategies=("predictive", "expert
         def run():
             for k in range(steps // every):
                 c, rep = s.autotune(strategy=strat, trial_steps=5, probe_steps=2, probe_factor=2.0,
-                                    skip_within=skip_within)
+                                    skip_within=skip_within, forest_top=top)
                 s.step(every - rep["trial_steps_total"])
                 phases.append({"step": k * every, "chosen": c.name(), "ntrialled": rep["ntrialled"],
                                "skipped": rep["skipped"], "phase_ms": rep["phase_ms"],
@@ -338,6 +339,8 @@ def inhomogeneous_leg(steps=20000, every=1000, strategies=("predictive", "expert
             f.close()
 
     others = {st: tuned_run(st) for st in strategies}
+    # the forest's three most probable classes trialled in each phase
+    others["forest_top3"] = tuned_run("forest", 3)
     forest_runs = [tuned_run("forest")]
     screen = min(steps, 1000 if fixed_steps is None else fixed_steps)
     screened = {c.name(): (c, run_fixed(c, screen)) for c in cands}
@@ -367,14 +370,18 @@ def inhomogeneous_leg(steps=20000, every=1000, strategies=("predictive", "expert
     return out
 
 
-def walled_leg(steps=150000, every=1000, thermo_every=100, d_t=0.1, target=100.0, strategies=("forest", "predictive")):
+def walled_leg(steps=150000, every=1000, thermo_every=100, d_t=0.1, target=100.0,
+               strategies=(("forest", "forest", 1), ("forest_top3", "forest", 3), ("predictive", "predictive", 1),
+                           ("expert", "expert", 1)), repeats=3):
     """The walled heating sphere of Sec. 6 (5497 particles in a 200^3 box with
     reflective walls, cutoff 3, skin 0.5, R 10, dt 1e-4): every thermo_every
     steps a velocity-scaling thermostat moves T by at most d_t towards
     target; every `every` steps a tuning phase re-selects the configuration
     (its trial steps count as steps).  Each strategy's run and every fixed
     configuration run the same schedule from the same state; times are CUDA
-    events on the system's stream around the whole run."""
+    events on the system's stream around the whole run.  The Random Forest
+    run (its first choice each phase) and the two best fixed configurations
+    run `repeats` times, alternating, and compare by medians."""
     import torch
 
     import paper_2505_03438_gb300 as lj
@@ -384,11 +391,11 @@ def walled_leg(steps=150000, every=1000, thermo_every=100, d_t=0.1, target=100.0
     n = len(sc["x"])
     stream = torch.cuda.current_stream()
 
-    def schedule(s, strategy=None, phases=None):
+    def schedule(s, strategy=None, phases=None, top=1):
         done, next_tune = 0, 0
         while done < steps:
             if strategy and done >= next_tune:
-                c, rep = s.autotune(strategy=strategy, trial_steps=5, probe_steps=2, probe_factor=2.0)
+                c, rep = s.autotune(strategy=strategy, trial_steps=5, probe_steps=2, probe_factor=2.0, forest_top=top)
                 done += rep["trial_steps_total"]
                 phases.append((done, c.name(), rep["ntrialled"]))
                 next_tune += every
@@ -411,35 +418,50 @@ def walled_leg(steps=150000, every=1000, thermo_every=100, d_t=0.1, target=100.0
     out = {"workload": "walled_heating_sphere: N=%d, box 200 with reflective walls, rc 3, skin 0.5, R 10, dt 1e-4, "
                        "thermostat every %d steps by <= %g towards T %g, re-tune every %d" %
                        (n, thermo_every, d_t, target, every), "steps": steps}
-    for strat in strategies:
+    def tuned(label, strat, top):
         s = lj.System(sc, stream=stream.cuda_stream)
         if strat == "forest":
             s.set_forest()
         phases = []
-        ms, done = timed(lambda: schedule(s, strat, phases))
+        ms, done = timed(lambda: schedule(s, strat, phases, top))
         t_end = s.thermostat(target, 0.0)
         # the phases where the choice changed
         changes = [p for k, p in enumerate(phases) if k == 0 or p[1] != phases[k - 1][1]]
-        out[strat] = {"value": n * done / (ms * 1e-3), "steps": done, "final_T": t_end,
-                      "trials": sum(p[2] for p in phases), "choice_changes": changes[:40]}
         s.close()
-    probe = lj.System(sc)
-    cands = lj.ljsel_default_candidates(probe.h)
-    probe.close()
-    fixed = {}
-    for c in cands:
+        return {"value": n * done / (ms * 1e-3), "steps": done, "final_T": t_end,
+                "trials": sum(p[2] for p in phases), "choice_changes": changes[:40]}
+
+    def run_fixed(c):
         f = lj.System(sc, stream=stream.cuda_stream)
         try:
             lj.ljsel_set_config(f.h, c)
             ms, done = timed(lambda: schedule(f))
-            fixed[c.name()] = n * done / (ms * 1e-3)
+            return n * done / (ms * 1e-3)
         except lj.LjselError:
-            pass
+            return None
         finally:
             f.close()
-    best = max(fixed.items(), key=lambda kv: kv[1]) if fixed else None
-    out.update({"fixed": fixed, "best_fixed": best,
-                "tuned_over_best_fixed": {k: out[k]["value"] / best[1] for k in strategies} if best else None})
+
+    for label, strat, top in strategies:
+        out[label] = tuned(label, strat, top)
+    probe = lj.System(sc)
+    cands = {c.name(): c for c in lj.ljsel_default_candidates(probe.h)}
+    probe.close()
+    fixed = {k: v for k, v in ((name, run_fixed(c)) for name, c in cands.items()) if v is not None}
+    runs = {k: [fixed[k]] for k in sorted(fixed, key=lambda k: -fixed[k])[:2]}
+    forest_runs = [out["forest"]["value"]] if "forest" in out else []
+    for _ in range(repeats - 1):
+        if forest_runs:
+            forest_runs.append(tuned("forest", "forest", 1)["value"])
+        for k in runs:
+            runs[k].append(run_fixed(cands[k]))
+    med = {k: statistics.median(v) for k, v in runs.items()}
+    best = max(med.items(), key=lambda kv: kv[1]) if med else None
+    ratios = {label: out[label]["value"] / best[1] for label, _, _ in strategies} if best else None
+    if best and forest_runs:
+        out["forest"]["values"] = forest_runs
+        ratios["forest"] = statistics.median(forest_runs) / best[1]
+    out.update({"fixed": fixed, "fixed_reruns": runs, "best_fixed": best, "tuned_over_best_fixed": ratios})
     return out
 
 
@@ -551,9 +573,9 @@ def run_ours(args):
     ms, steps_done, chosen, rep = run["ms"], run["steps"], run["chosen"], run["rep"]
     value = job_throughput(world, n, steps_done, ms)
     chosen_name = chosen.name()
-    # further tuned runs, for a median against the best fixed configuration
     tuned_values = [value]
-    for _ in range(max(0, args.repeats - 1)):
+
+    def tuned_again():
         hx = fresh()
         r = timed(hx, headline)
         tuned_values.append(job_throughput(world, n, r["steps"], r["ms"]))
@@ -564,8 +586,12 @@ def run_ours(args):
     _, npairs = lj.ljsel_get_pairs(h, 0)
     cnt = lj.ljsel_get_counters(h)
 
-    # ---- every fixed configuration from the same initial state, the same
-    # warm-up and the same K timed steps; the best three again, repeatedly
+    # ---- every fixed configuration from the same initial state and the same
+    # warm-up, then K timed steps that, like the tuned run's, include the
+    # build of the configuration's neighbour structure (the state is set again
+    # after the warm-up, which asks for a rebuild); the best three again,
+    # alternating with further tuned runs, so that a drift of the GPU's speed
+    # over the run weighs on both sides alike
     fixed, fixed_eff, best = {}, {}, None
     if args.fixed_steps != 0:
         kf = K if args.fixed_steps < 0 else args.fixed_steps
@@ -575,6 +601,7 @@ def run_ours(args):
             lj.ljsel_set_state(h, x, v)
             lj.ljsel_set_config(h, c)
             lj.ljsel_step(h, W)
+            lj.ljsel_set_state(h, x, v)
             torch.cuda.synchronize()
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
@@ -594,9 +621,19 @@ def run_ours(args):
             slots = ct["list_entries"] * (c.cluster_size if c.method == lj.METHOD_CLUSTER else 1)
             fixed_eff[name] = (np_c * (1 if c.newton3 else 2) / slots) if slots else None
         top = sorted(fixed, key=lambda k: -fixed[k])[:3]
-        remeasured = {k: statistics.median([run_fixed(cands[k]) for _ in range(max(1, args.repeats))]) for k in top}
+        runs = {k: [] for k in top}
+        for rr in range(max(1, args.repeats)):
+            if rr > 0 and headline is not None:
+                tuned_again()
+            for k in top:
+                runs[k].append(run_fixed(cands[k]))
+        remeasured = {k: statistics.median(vv) for k, vv in runs.items()}
         bname = max(remeasured, key=remeasured.get)
         best = {"name": bname, "value": remeasured[bname], "steps": kf, "remeasured_top3": remeasured}
+    else:
+        for _ in range(max(0, args.repeats - 1)):
+            if headline is not None:
+                tuned_again()
     lj.ljsel_destroy(h)
 
     # ---- end to end through the C ABI with pinned host buffers ------------

@@ -312,7 +312,8 @@ def training_scenarios(seed=7, dmin=0.9, rc=2.5, dt=0.005, rebuild=10):
     """Synthetic scenarios for the data behind the Random Forest strategy, of
     the paper's kinds (Sec. 5.3: uniform gases, clustered particles, a dense
     cuboid in a gas, spheres in a large box, an almost empty box), scaled to
-    r_c = 2.5 and to sizes of 10^3 to 4.4 x 10^5 particles.  Placement keeps
+    r_c = 2.5 and to sizes of 10^3 to 4.4 x 10^5 particles, and spheres in
+    large boxes with reflective walls at the paper's heating-run settings.  Placement keeps
     a minimum spacing dmin so that trial steps stay physical; skins cycle
     through 0.1 ... 0.5 as in the paper's data.  Yields scenario dicts."""
     rng = np.random.default_rng(seed)
@@ -369,3 +370,23 @@ def training_scenarios(seed=7, dmin=0.9, rc=2.5, dt=0.005, rebuild=10):
     # an almost empty box
     x = _rsa(np.full(3, 20.0), 0.0, 40.0, 50, dmin, rng, inside=False)
     yield make("empty_L40", x, 40.0, 1.0)
+    # spheres in a large box closed by reflective walls, as in the paper's
+    # heating run (Sec. 6.1: cutoff 3, skin 0.5, dt 1e-4): condensed fcc balls
+    # (density 0.8442) of 2,000 to 16,000 particles, and clouds of 5,000
+    # particles spread over a larger radius (the later, evaporated stages)
+    def walled(name, x, box_len, temperature):
+        sc = make(name, x, box_len, temperature)
+        sc.update(_single_type(np.full(3, box_len), 3.0))
+        sc.update(dt=1e-4, skin=0.5, walls=(1, 1, 1))
+        return sc
+
+    for n_ball, box_len, temperature in ((2000, 100.0, 0.1), (4000, 200.0, 1.0), (8000, 150.0, 0.5),
+                                         (16000, 250.0, 2.0)):
+        m = int(math.ceil((2.0 * n_ball / 4.0) ** (1.0 / 3.0))) + 2
+        lat, lbox = fcc_lattice(m, 0.8442)
+        c = lat - 0.5 * lbox
+        x = c[np.argsort((c * c).sum(1), kind="stable")[:n_ball]] + 0.5 * box_len
+        yield walled("wball_N%d_L%g" % (n_ball, box_len), x, box_len, temperature)
+    for radius, temperature in ((20.0, 20.0), (40.0, 40.0), (60.0, 60.0)):
+        x = _rsa(np.full(3, 100.0), radius, 200.0, 5000, dmin, rng, inside=True, min_batch=2000)
+        yield walled("wcloud_R%g" % radius, x, 200.0, temperature)

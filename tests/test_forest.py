@@ -113,11 +113,12 @@ def test_training_scenarios_are_physical_inputs():
     inside its box, no two closer than the 0.9 spacing outside the jittered
     lattices (whose nearest neighbours sit at a/sqrt(2) - 0.1*sqrt(3) or
     more), zero momentum and the drawn temperature exactly, boxes that admit
-    the minimum image at the scenario's skin, skins cycling 0.1 ... 0.5."""
+    the minimum image at the scenario's skin, skins cycling 0.1 ... 0.5 (the
+    walled spheres at the heating run's settings)."""
     from scipy.spatial import cKDTree
 
     from paper_2505_03438_gb300 import scenarios
-    seen = []
+    seen, walled = [], []
     for sc in scenarios.training_scenarios():
         x, v, L = sc["x"], sc["v"], sc["box"][0]
         n = len(x)
@@ -130,7 +131,12 @@ def test_training_scenarios_are_physical_inputs():
             assert np.abs(v.sum(0)).max() < 1e-9 * n, sc["name"]
             assert abs((v * v).sum() / (3 * n - 3) - sc["temperature"]) < 1e-9, sc["name"]
         seen.append((sc["name"], sc["skin"]))
-    assert len(seen) == 42
+        if sc.get("walls"):
+            assert sc["skin"] == 0.5 and sc["dt"] == 1e-4 and float(np.max(sc["rcut"])) == 3.0, sc["name"]
+            walled.append((sc["name"], n, L))
+    assert len(seen) == 49
     assert [s for _, s in seen[:10]] == [0.1, 0.2, 0.3, 0.4, 0.5] * 2
-    # the benchmark workloads are not among them
+    # the benchmark workloads are not among them (the walled heating run is
+    # 5497 particles in a box of 200)
     assert not any(nm.startswith("fcc_n64") or nm.startswith("heated") for nm, _ in seen)
+    assert len(walled) == 7 and not any(n == 5497 for _, n, _ in walled)

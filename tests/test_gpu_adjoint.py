@@ -6,8 +6,10 @@ for the element-wise and finite-difference checks, the full 32^3 lattice
 (N = 32,768) for parity at size.  The pair mask is frozen at every
 evaluation point on both sides.  FP64 path: equal to the oracle's analytic
 gradient within 1e-10 (one step) / 1e-9 (50 steps) relative, and to central
-differences (h = 1e-6) within 1e-6.  FP32 path: its error against the FP64
-oracle is bounded here and reported by the assertion messages.
+differences (h = 1e-6) within 1e-6.  FP32 path: the 50-step rollout
+gradient within 5e-4 relative of the FP64 oracle (measured about 5e-5: FP32
+rounding of the forces, 1e-6 relative, grows through the chaotic dynamics
+over 0.25 time units; the bar leaves a factor 10).
 """
 import numpy as np
 import pytest
@@ -176,7 +178,7 @@ def test_rollout_gradient_matches_oracle(small_rollout_oracle, precision):
     sc, (FstarN, ref) = small_rollout_oracle
     s = lj.System(sc, precision=precision)
     got = _rollout_grads(s, sc, 50, 10, FstarN)
-    tol = 1e-9 if precision else 2e-3
+    tol = 1e-9 if precision else 5e-4
     assert abs(got[0] - ref[0]) < tol * ref[0], (got[0], ref[0])
     for name, a, b in zip(("x0", "v0", "theta"), got[1:], ref[1:]):
         assert _rel(a, b) < tol, (name, _rel(a, b))
@@ -220,7 +222,7 @@ def test_rollout_gradient_full_size():
     oracle's analytic gradient, FP32 path error bounded."""
     sc = _case("full")
     FstarN, ref = _oracle_rollout(sc, 50)
-    for precision, tol in ((1, 1e-9), (0, 2e-3)):
+    for precision, tol in ((1, 1e-9), (0, 5e-4)):
         s = lj.System(sc, precision=precision)
         got = _rollout_grads(s, sc, 50, 10, FstarN)
         assert abs(got[0] - ref[0]) < tol * ref[0], (precision, got[0], ref[0])
