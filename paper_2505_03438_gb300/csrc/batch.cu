@@ -30,6 +30,7 @@
 
 #include "kernels.cuh"
 #include "system.h"
+#include "update.cuh"
 
 using namespace ljsel;
 
@@ -461,18 +462,30 @@ __global__ void __launch_bounds__(256) k_bforce(BDev<R> S, int2 *pairs3, long lo
             }
             continue;
         }
-        // leapfrog Stormer-Verlet: v += (dt/m) F (dt/2m at the integer step), x += dt v
+        // leapfrog Stormer-Verlet: v += (dt/m) F (dt/2m at the integer step),
+        // x += dt v; every load before the stores (which may alias them as
+        // far as the compiler knows), the FP32 <-> FP64 conversions on the
+        // integer pipes
         const int n = S.ntot;
         double *X = S.x[sp], *V = S.v[sp];
+        const double v0x = V[i], v0y = V[n + i], v0z = V[2 * n + i];
+        const double x0 = X[i], y0 = X[n + i], z0 = X[2 * n + i];
+        const V4<R> r0 = S.xref[i];
         R c = S.inv_mass_dt;
         if (C->half_kick) c *= (R)0.5;
-        double vx = V[i] + (double)(c * fx), vy = V[n + i] + (double)(c * fy), vz = V[2 * n + i] + (double)(c * fz);
-        const double x = fma(S.dt, vx, X[i]), y = fma(S.dt, vy, X[n + i]), z = fma(S.dt, vz, X[2 * n + i]);
+        double vx, vy, vz;
+        if constexpr (sizeof(R) == 4) {
+            vx = v0x + f32_to_f64(c * fx); vy = v0y + f32_to_f64(c * fy); vz = v0z + f32_to_f64(c * fz);
+        } else {
+            vx = v0x + c * fx; vy = v0y + c * fy; vz = v0z + c * fz;
+        }
+        const double x = fma(S.dt, vx, x0), y = fma(S.dt, vy, y0), z = fma(S.dt, vz, z0);
         V[i] = vx; V[n + i] = vy; V[2 * n + i] = vz;
         X[i] = x; X[n + i] = y; X[2 * n + i] = z;
-        const V4<R> nw = make_pos((R)x, (R)y, (R)z, 0);
+        V4<R> nw;
+        if constexpr (sizeof(R) == 4) nw = make_pos(f64_to_f32(x), f64_to_f32(y), f64_to_f32(z), 0);
+        else nw = make_pos(x, y, z, 0);
         S.pos[pp ^ 1][i] = nw;
-        const V4<R> r0 = S.xref[i];
         const R ddx = nw.x - r0.x, ddy = nw.y - r0.y, ddz = nw.z - r0.z;
         if (!(ddx * ddx + ddy * ddy + ddz * ddz < S.half_skin2)) {
             exceeded = true;
