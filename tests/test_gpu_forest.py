@@ -32,10 +32,12 @@ def test_forest_strategy_trials_the_forests_first_choices():
     m = forest.load()
     s.set_forest(m)
     trialled = selected = 0
+    blacklist = set()  # configurations a trial measured 10x slower than the best (the default factor)
     for phase, top in enumerate((1, 1, 3, 2)):
         st = s.stats()
         p = forest.predict_proba(m, [st[k] for k in forest.FEATURES])
-        expect = [m["classes"][k] for k in np.argsort(-p, kind="stable")[:top]]
+        ranked = [m["classes"][k] for k in np.argsort(-p, kind="stable")]
+        expect = [nm for nm in ranked if nm not in blacklist][:top] if top > 1 else ranked[:1]
         before = s.config().name()
         c, rep = s.autotune(strategy="forest", trial_steps=4, forest_top=top)
         assert rep["expert_input"] == p.max() and rep["phase"] == phase + 1
@@ -50,6 +52,8 @@ def test_forest_strategy_trials_the_forests_first_choices():
         trialled += top
         assert sorted(costs) == sorted(expect)
         assert c.name() == min(costs, key=costs.get) and s.config().name() == c.name()
+        best = min(costs.values())
+        blacklist |= {nm for nm, v in costs.items() if v > 10.0 * best}
     assert selected == 2
     nsteps = s.counters()["steps"]
     assert nsteps == 4 * trialled
