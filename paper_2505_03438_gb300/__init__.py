@@ -526,10 +526,20 @@ def ljsel_predictive_trials(phase, history, last_trial_phase, blacklisted, incum
     return out[:n].tolist()
 
 
+_FOREST_STRUCTS = {}
+
+
 def _forest_struct(model):
     """ljsel_forest over the arrays of a forest model (dict of numpy arrays,
     see paper_2505_03438_gb300.forest); the arrays are kept alive on the
-    returned struct."""
+    returned struct.  The struct of a model object is built once (turning a
+    loaded model's lists into arrays takes longer than a short run's steps)
+    and rebuilt when one of its arrays is replaced."""
+    key = id(model)
+    ids = tuple(id(model[k]) for k in ("root", "feature", "threshold", "left", "right", "value", "classes"))
+    hit = _FOREST_STRUCTS.get(key)
+    if hit is not None and hit[0] is model and hit[1] == ids:
+        return hit[2]
     keep = {
         "root": np.ascontiguousarray(model["root"], np.int32),
         "feature": np.ascontiguousarray(model["feature"], np.int32),
@@ -549,6 +559,9 @@ def _forest_struct(model):
         setattr(f, k, a.ctypes.data)
     f.classes = cls
     f._keep = (keep, cls)
+    if len(_FOREST_STRUCTS) > 8:
+        _FOREST_STRUCTS.clear()
+    _FOREST_STRUCTS[key] = (model, ids, f)
     return f
 
 

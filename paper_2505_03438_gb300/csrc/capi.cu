@@ -395,18 +395,7 @@ ljsel_status ljsel_create(const ljsel_params *params, int64_t n, const double *p
     if (st != LJSEL_OK) return fail(st);
     st = s->apply_config();
     if (st != LJSEL_OK) return fail(st);
-    // type check and staging of host inputs
-    std::vector<int32_t> ht;
-    if (types) {
-        ht.resize(n);
-        if (on_device) {
-            if (cudaMemcpy(ht.data(), types, n * 4, cudaMemcpyDeviceToHost) != cudaSuccess) { set_error("types copy failed"); return fail(LJSEL_ERR_CUDA); }
-        } else {
-            memcpy(ht.data(), types, n * 4);
-        }
-        for (int64_t i = 0; i < n; ++i)
-            if (ht[i] < 0 || ht[i] >= params->ntypes) { set_error("a type is outside [0, ntypes)"); return fail(LJSEL_ERR_ARG); }
-    }
+    // staging of host inputs (the import kernel checks the types)
     const size_t nb = (size_t)n * 3 * sizeof(double);
     const double *dpos = pos, *dvel = vel;
     const int32_t *dtyp = types;
@@ -440,7 +429,8 @@ ljsel_status ljsel_create(const ljsel_params *params, int64_t n, const double *p
     st = s->cmd(CMD_INTERVAL, s->cfg.rebuild_interval);
     if (st == LJSEL_OK) st = s->cmd(CMD_REBUILD, 0);
     if (st == LJSEL_OK) st = s->cmd(CMD_HALF_KICK, 1);
-    if (st == LJSEL_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) { set_error(cudaGetErrorString(cudaGetLastError())); st = LJSEL_ERR_CUDA; }
+    if (st == LJSEL_OK) st = s->read_ctrl();  // synchronizes
+    if (st == LJSEL_OK && s->h_ctrl->bad_type) { set_error("a type is outside [0, ntypes)"); st = LJSEL_ERR_ARG; }
     if (st != LJSEL_OK) return fail(st);
     *out = reinterpret_cast<ljsel_system>(s);
     return LJSEL_OK;

@@ -390,7 +390,12 @@ __global__ void k_import_state(Dev<R> S, const double *pos, const double *vel, c
     const int sp = C->state_par, pp = C->pos_par, n = S.n;
     if (init_ids) {
         S.id[sp][i] = i;
-        S.type[sp][i] = types ? types[i] : 0;
+        int t = types ? types[i] : 0;
+        if (t < 0 || t >= S.tab.ntypes) {  // reported by the creating call
+            C->bad_type = 1;
+            t = 0;
+        }
+        S.type[sp][i] = t;
     }
     const int id = S.id[sp][i];
     double x[3];

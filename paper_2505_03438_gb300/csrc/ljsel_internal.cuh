@@ -115,6 +115,7 @@ struct Ctrl {
     int64_t replica_rebuilds;  // batches: replica rebuilds summed over replicas
     int32_t check_failed;      // checked build: an index fell outside its array
     int32_t check_site;        // checked build: the first failing site (CHECK_* code)
+    int32_t bad_type;          // an imported particle type lies outside [0, ntypes)
 };
 
 // Bounds checks of the checked build (compiled with -DLJSEL_CHECK): an index

@@ -49,22 +49,48 @@ const char *last_error() { return g_last_error.c_str(); }
 // ---------------------------------------------------------------------------
 // Device buffers
 
+// Device buffers come from the device's default memory pool, which is told
+// once per device to keep up to 8 GB of freed memory for reuse: a system
+// created after another was destroyed then takes its buffers from the pool
+// instead of the driver (a cudaMalloc or cudaFree of a large buffer costs
+// tens to hundreds of microseconds and a cudaFree synchronizes the device).
+// Allocations and frees are ordered on the legacy default stream and waited
+// for, so a buffer is ready on any stream when ensure returns, and a freed
+// one is reused only after the work that used it (every caller synchronizes
+// its stream before it regrows or releases a buffer).
+static ljsel_status pool_once() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LJSEL_OK;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return LJSEL_OK;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = 8ull << 30;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    done[dev] = true;
+    return LJSEL_OK;
+}
+
 ljsel_status Buf::ensure(size_t bytes) {
     if (bytes <= size) return LJSEL_OK;
-    if (ptr) cudaFree(ptr);
-    ptr = nullptr;
-    size = 0;
-    cudaError_t e = cudaMalloc(&ptr, bytes ? bytes : 16);
+    release();
+    pool_once();
+    cudaError_t e = cudaMallocAsync(&ptr, bytes ? bytes : 16, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) {
+        if (ptr) cudaFreeAsync(ptr, 0);
         ptr = nullptr;
-        set_error(std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
-        return LJSEL_ERR_OOM;
+        set_error(std::string("allocation of ") + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? LJSEL_ERR_OOM : LJSEL_ERR_CUDA;
     }
     size = bytes;
     return LJSEL_OK;
 }
 void Buf::release() {
-    if (ptr) cudaFree(ptr);
+    if (ptr) cudaFreeAsync(ptr, 0);
     ptr = nullptr;
     size = 0;
 }

@@ -5,6 +5,7 @@
 * Non-finite input (injected on the host) is reported as
   LJSEL_ERR_NONFINITE by the device flags, never trapped.
 * A checkpoint written to .npz resumes the FP64 trajectory.
+* Particle types outside the parameter table are refused at creation.
 """
 import numpy as np
 import pytest
@@ -56,3 +57,18 @@ def test_checkpoint_resumes_the_trajectory(tmp_path):
     d = xa - xb
     d -= L * np.round(d / L)
     assert np.abs(d).max() < 1e-10 and np.abs(va - vb).max() < 1e-10
+
+
+@pytest.mark.parametrize("bad", [2, -1])
+def test_types_outside_the_table_are_refused(bad):
+    """The import kernel checks every type against [0, ntypes); the creating
+    call reports LJSEL_ERR_ARG and frees what it allocated."""
+    sc = scenarios.binary_mixture(seed=14, nside=7)
+    t = np.asarray(sc["types"], np.int32).copy()
+    t[len(t) // 2] = bad
+    with pytest.raises(lj.LjselError) as e:
+        lj.System(dict(sc, types=t))
+    assert e.value.status == 1 and "ntypes" in lj.ljsel_last_error()
+    s = lj.System(sc)  # the valid input still works
+    s.compute()
+    s.close()
