@@ -155,9 +155,10 @@ def step_roofline(n, npairs, n3l, entries, ncell, rebuild_every, peaks, hbm_gbs)
             "rebuild_us": 1e6 * t_rebuild, "rebuild_every": rebuild_every}
 
 
-def oracle_rate(sc, budget_s=12.0):
+def oracle_rate(sc, budget_s=12.0, single=False):
     """The FP64 oracle (linked cells, OpenMP on all host cores) advancing a
-    bounded number of Stormer-Verlet steps of the same system."""
+    bounded number of Stormer-Verlet steps of the same system; with single,
+    also one thread on a smaller sample of the same liquid."""
     import oracle
     cores = len(os.sched_getaffinity(0))
     p = oracle.make_params(sc["box"], sc["eps"], sc["sigma"], sc["rcut"], True)
@@ -172,10 +173,23 @@ def oracle_rate(sc, budget_s=12.0):
                       nthreads=cores)
     t1 = time.perf_counter()
     n = len(sc["x"])
-    return {"value": n * nsteps / (t1 - t0), "unit": UNIT, "cores": cores, "kind": "oracle", "steps": nsteps,
-            "seconds": t1 - t0,
-            "sample": "%d Stormer-Verlet steps of the N=%d liquid (FP64 linked cells, %d OpenMP threads)" %
-                      (nsteps, n, cores)}
+    out = {"value": n * nsteps / (t1 - t0), "unit": UNIT, "cores": cores, "kind": "oracle", "steps": nsteps,
+           "seconds": t1 - t0,
+           "sample": "%d Stormer-Verlet steps of the N=%d liquid (FP64 linked cells, %d OpenMP threads)" %
+                     (nsteps, n, cores)}
+    if single:
+        # one thread, on a 2-step sample of the first 131,072 particles of
+        # the same lattice in a box of the same density (fcc 32^3 x 4)
+        from paper_2505_03438_gb300 import scenarios
+        small = scenarios.fcc_liquid(32, density=0.8442, temperature=0.72, seed=2)
+        ps = oracle.make_params(small["box"], small["eps"], small["sigma"], small["rcut"], True)
+        t0 = time.perf_counter()
+        oracle.verlet_run(small["x"], small["v"], None, small["mass"], ps, small["dt"], 2, cell_min=cell_min, nthreads=1)
+        t1 = time.perf_counter()
+        m = len(small["x"])
+        out["single_thread"] = {"value": m * 2 / (t1 - t0), "cores": 1, "seconds": t1 - t0,
+                                "sample": "2 Stormer-Verlet steps of the same liquid at N=%d (fcc 32^3 x 4), one thread" % m}
+    return out
 
 
 def adjoint_leg(reps=20, nsteps=50, every=10):
@@ -713,7 +727,7 @@ def emit(args, L):
                       "ratio": tuned_med / best["value"], "repeats": args.repeats, "steps": K}
     cb = None
     if args.cpu_baseline and world == 1:
-        cb = oracle_rate(sc)
+        cb = oracle_rate(sc, single=True)
     details = {"peaks_probe": peaks, "hbm_gbs": hbm, "fixed": L["fixed"], "fixed_pair_efficiency": L["fixed_eff"],
                "best_fixed": best, "tuned_values": L["tuned_values"], "other_tuned_runs": L["extra_runs"],
                "tuner": dict(rep, strategy=L["headline"]) if rep else None,
