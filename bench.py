@@ -50,21 +50,25 @@ WORKLOAD = "lj_liquid_1m: N=1048576 fcc 64^3x4, rho 0.8442, T 0.72, rc 2.5, skin
 FLOPS_PER_PAIR = 28
 # Algorithmic per-particle figures of the other kernels of a step:
 # the Stormer-Verlet update reads and writes the FP64 x, v (96 B), writes the
-# FP32 working position (16 B) and reads the force (16 B), and issues about
-# 12 FP64 instructions (3 conversions and 3 adds for v, 3 fused multiply-adds
-# for x, 3 conversions to FP32); a rebuild reads the working position and
+# FP32 working position (16 B) and reads the force (16 B), and issues 6 FP64
+# instructions (3 adds for v, 3 fused multiply-adds for x; the FP32 <-> FP64
+# conversions run on the integer pipes); a rebuild reads the working position and
 # writes the sorted one and the permutation (36 B), 8 B per cell, reads the
 # position once more for the lists (16 B) and writes 4 B per list entry.
 UPDATE_BYTES_PER_PARTICLE = 128
-UPDATE_FP64_PER_PARTICLE = 12
+UPDATE_FP64_PER_PARTICLE = 6
 REBUILD_BYTES_PER_PARTICLE = 36 + 16
 REBUILD_BYTES_PER_CELL = 8
 LIST_BYTES_PER_ENTRY = 4
-# DRAM bytes (read + write) of one launch of the Verlet-list force kernel fused
-# with the update (N3L off, two lanes per particle), N = 1,048,576, from an
-# ncu capture of that kernel; reported only when that configuration is the
-# chosen one.
-VL_T2_TRAFFIC_1M = {"config": "VL-noN3L-t2", "bytes": 491916288 + 57595648}
+# DRAM bytes (read + write) of one launch of the force kernel (fused with the
+# update when N3L is off) at N = 1,048,576, CSF 1, from ncu captures of those
+# kernels; reported only when the chosen configuration is one of them.
+FORCE_TRAFFIC_1M = {
+    "VL-noN3L-t2": 491916288 + 57595648,
+    "VL-N3L-t4": 340648192 + 15194368,
+    "CL4-noN3L-t4": 283816960 + 19887360,
+    "CL4-N3L-t8": 145644800 + 6951936,
+}
 
 
 def max_over_ranks(ms, dist=None, device="cpu"):
@@ -703,11 +707,10 @@ def emit(args, L):
     force_ms = prof["force_ms"]
     achieved = npairs * FLOPS_PER_PAIR / (force_ms * 1e-3) / 1e12 if force_ms > 0 else None
     base = "-".join(chosen_name.split("-")[:3])
-    traffic = VL_T2_TRAFFIC_1M["bytes"] if (base == VL_T2_TRAFFIC_1M["config"] and chosen.csf == 1.0 and
-                                            n == 1048576) else None
+    traffic = FORCE_TRAFFIC_1M.get(base) if (chosen.csf == 1.0 and n == 1048576) else None
     roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": (achieved / fp32_peak) if achieved else None, "traffic": traffic,
-            "traffic_source": ("ncu capture of %s at N = 1,048,576" % VL_T2_TRAFFIC_1M["config"]) if traffic else None,
+            "traffic_source": ("ncu capture of %s at N = 1,048,576" % base) if traffic else None,
             "kernel": "force (%s)" % chosen_name, "launch_ms": force_ms,
             "flops_per_launch": npairs * FLOPS_PER_PAIR, "peak_basis": "of measured (FP32 probe)"}
     # ---- step roofline -------------------------------------------------------
