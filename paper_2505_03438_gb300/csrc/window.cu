@@ -228,7 +228,7 @@ __device__ bool load_window(const Dev<R> &S, Win<R, G, F> &win, int row, int x0,
         if (G) win.gidx[WIN_CAP] = -1;
         if (F) win.frc[WIN_CAP] = make_pos((R)0, (R)0, (R)0, 0);
     }
-    // one verdict for the whole block, so that a timeout ends every thread
+    // one decision for the whole block, so that a timeout ends every thread
     const bool ok = __syncthreads_and(mbar_wait(&win.mbar, win.phase)) != 0;
     if (threadIdx.x == 0) win.phase ^= 1;
     return ok;

@@ -90,3 +90,22 @@ def test_phase_skipped_while_statistics_hold():
     assert c2.name() == c1.name() and s.counters()["steps"] == steps
     c3, r3 = s.autotune(strategy="predictive", trial_steps=1, skip_within=0.0)
     assert r3["skipped"] == 0 and r3["phase"] == r1["phase"] + 1
+
+
+def test_tuning_cost_uses_the_observed_rebuild_interval():
+    """When most rebuilds since the last phase came early (a particle reached
+    skin/2 before R steps), the next phase weights build times by the
+    observed steps per rebuild instead of R (reported as rebuild_every)."""
+    sc = scenarios.heated_sphere(box_len=60.0, radius=15.0, seed=31)
+    s = lj.System(sc)
+    _, r1 = s.autotune(strategy="full", trial_steps=2)
+    assert r1["rebuild_every"] == 0.0  # no window yet
+    c1 = s.counters()
+    s.step(200)
+    c2 = s.counters()
+    dr, de = c2["rebuilds"] - c1["rebuilds"], c2["early_rebuilds"] - c1["early_rebuilds"]
+    _, r2 = s.autotune(strategy="full", trial_steps=2)
+    assert dr > 0 and 2 * de >= dr, (dr, de)  # the hot ball forces early rebuilds
+    assert abs(r2["rebuild_every"] - 200.0 / dr) < 1e-9, (r2["rebuild_every"], dr)
+    assert 0.0 < r2["rebuild_every"] < 20.0
+    s.close()
