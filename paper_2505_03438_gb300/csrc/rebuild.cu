@@ -23,6 +23,20 @@ constexpr unsigned long long VAL_MASK = (1ull << 62) - 1ull;
 constexpr int SPIN_LIMIT = 1 << 22;
 constexpr int VL_BUILD_THREADS = 128;
 constexpr int VL_BUILD_MIN_BLOCKS = 8;  // 32 warps per SM: at most 64 registers a thread
+constexpr int VL_WBUILD_THREADS = 256;  // eight particles a block in the warp-per-particle build
+// Small systems build their Verlet lists with a warp per particle, larger
+// ones with a thread per particle.  The limits are where the two measured
+// equal on a liquid at rho 0.8442: about 24k particles when the stencil is
+// 27 cells of side r_list (CSF 1), about 8k for 125 cells of half that side
+// (CSF 0.5), whose runs of five small cells leave more of a warp's lanes
+// idle.  Below them the one-thread build leaves most SMs with one or two
+// warps, each walking its candidates one load after another.
+#ifndef VL_WARP_BUILD_MAX_N
+#define VL_WARP_BUILD_MAX_N 24576
+#endif
+#ifndef VL_WARP_BUILD_MAX_N_HALF_CELLS
+#define VL_WARP_BUILD_MAX_N_HALF_CELLS 8192
+#endif
 
 __device__ __forceinline__ unsigned morton3(unsigned x, unsigned y, unsigned z) {
     unsigned k = 0;
@@ -371,6 +385,106 @@ __global__ void __launch_bounds__(VL_BUILD_THREADS, VL_BUILD_MIN_BLOCKS) k_vl_bu
     block_add_entries(C, (act && need <= cap) ? (unsigned)need : 0u);
 }
 
+// The same rows for small systems, one warp per sorted particle i: with
+// one thread per particle a system of a few thousand particles fills one
+// or two warps an SM, and each thread walks its ~10^3 candidates one load
+// after another.  Here lane t tests candidates j0 + t and j0 + 32 + t of a
+// run (both loads issued first), a ballot gives the warp the block's mask,
+// and each accepted lane stores its own entry.  The k-th entry without an
+// image goes where the per-thread build's shift queue puts it (position
+// 3 - k mod 4 of chunk k / 4), the k-th image entry to slot cap - 1 - k, and
+// the candidates are walked in the same order with the same test, so the
+// two builds write identical rows.
+template <typename R, bool N3L, int RCH>
+__global__ void __launch_bounds__(VL_WBUILD_THREADS) k_vl_build_warp(Dev<R> S) {
+    Ctrl *C = S.ctrl;
+    if (!C->rebuild_now) return;
+    const int lane = threadIdx.x & 31;
+    const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const bool act = i < S.n;  // uniform across the warp
+    const int ii = act ? i : S.n - 1;
+    const V4<R> *P = S.pos[C->pos_par];
+    const int nx = S.nc[0], ny = S.nc[1], nz = S.nc[2];
+    const int c = S.cell_sorted[ii];
+    const int cxy = c % (nx * ny);
+    const int cx = cxy % nx, cy = cxy / nx, cz = c / (nx * ny);
+    const int cap = S.nl_cap;
+    const V4<R> pi = P[ii];
+    uint32_t *rowp = S.nl + (size_t)ii * cap;
+    const uint32_t lt = (1u << lane) - 1u;
+    int nf = 0, nb = 0;
+    auto inside = [&](const V4<R> &q, R xs, R ys, R zs) -> bool {
+        if constexpr (sizeof(R) == 4) {
+            const float ex = xs - q.x, ey = ys - q.y, ez = zs - q.z;
+            return (__float_as_uint(fmaf(ez, ez, fmaf(ey, ey, fmaf(ex, ex, -(float)S.rlist2)))) >> 31) != 0;
+        } else {
+            return r2_of(xs - q.x, ys - q.y, zs - q.z) < S.rlist2;
+        }
+    };
+    auto take = [&](bool in, int j, uint32_t code) {
+        const uint32_t mask = __ballot_sync(0xffffffffu, in);
+        if (in) {
+            const int k = __popc(mask & lt);
+            if (code == 0) {
+                const int e = nf + k, pos = (e & ~3) + 3 - (e & 3);
+                if (pos < cap) rowp[pos] = (uint32_t)j;
+            } else {
+                const int e = nb + k;
+                if (e < cap) rowp[cap - 1 - e] = (uint32_t)j | (code << JBITS);
+            }
+        }
+        if (code == 0) nf += __popc(mask);
+        else nb += __popc(mask);
+    };
+    for (int dz = N3L ? 0 : -RCH; dz <= RCH; ++dz) {
+        int wz, sz;
+        if (!stencil_cell(cz, dz, nz, S.walls[2], wz, sz)) continue;
+        for (int dy = -RCH; dy <= RCH; ++dy) {
+            if (N3L && dz == 0 && dy < 0) continue;
+            const bool own_row = dz == 0 && dy == 0;
+            int wy, sy;
+            if (!stencil_cell(cy, dy, ny, S.walls[1], wy, sy)) continue;
+            int xa = cx - RCH, xb = cx + RCH;
+            if (S.walls[0]) { xa = max(xa, 0); xb = min(xb, nx - 1); }
+            if (N3L && own_row) xa = cx;
+            const int rowc = (wz * ny + wy) * nx;
+            for (int sx = -1; sx <= 1; ++sx) {
+                const int a = sx < 0 ? xa : (sx == 0 ? max(xa, 0) : max(xa, nx));
+                const int b = sx < 0 ? min(xb, -1) : (sx == 0 ? min(xb, nx - 1) : xb);
+                if (a > b) continue;
+                int jb = S.cell_start[rowc + a - sx * nx];
+                const int je = S.cell_start[rowc + b - sx * nx + 1];
+                if (N3L && own_row && sx == 0) jb = ii + 1;
+                const uint32_t code = encode_image(sx, sy, sz);
+                const bool self = !N3L && code == 0 && jb <= ii && ii < je;
+                const R xs = pi.x - (R)sx * S.box[0], ys = pi.y - (R)sy * S.box[1], zs = pi.z - (R)sz * S.box[2];
+                for (int j0 = jb; j0 < je; j0 += 64) {
+                    const int ja = j0 + lane, jc = j0 + 32 + lane;
+                    const bool va = act && ja < je, vc = act && jc < je;
+                    const V4<R> qa = ldpos(P, va ? ja : ii), qc = ldpos(P, vc ? jc : ii);
+                    take(va && inside(qa, xs, ys, zs) && !(self && ja == ii), ja, code);
+                    if (j0 + 32 < je) take(vc && inside(qc, xs, ys, zs) && !(self && jc == ii), jc, code);
+                }
+            }
+        }
+    }
+    const int need = ((nf + 3) & ~3) + nb;
+    if (act) {
+        if (need > cap || nb > 0xffff || nf > 0xffff) {
+            if (lane == 0) {
+                C->overflow = 1;
+                S.nl_count[i] = 0;
+            }
+        } else {
+            const int r = nf & 3;
+            if (r && lane >= r && lane < 4) rowp[(nf & ~3) + 3 - lane] = (uint32_t)S.n;  // sentinel padding
+            if (lane == 0) S.nl_count[i] = nf | (nb << 16);
+        }
+    }
+    block_need_max(C, act ? (unsigned)need : 0u);
+    block_add_entries(C, (act && lane == 0 && need <= cap) ? (unsigned)need : 0u);
+}
+
 // Clusters: each cell's segment is cut into chunks of M consecutive sorted
 // particles (the last may be shorter); one thread per cell writes its
 // clusters' first particle, size and cell.
@@ -417,6 +531,17 @@ template <typename R> void launch_sortgather(const Dev<R> &S, cudaStream_t st) {
     k_sortgather<R><<<div_up(S.n, 256), 256, 0, st>>>(S);
 }
 template <typename R> void launch_vl_build(const Dev<R> &S, bool n3l, cudaStream_t st) {
+    if (S.n <= (S.reach == 1 ? VL_WARP_BUILD_MAX_N : VL_WARP_BUILD_MAX_N_HALF_CELLS)) {
+        const int wblocks = div_up(S.n, VL_WBUILD_THREADS / 32);
+        if (S.reach == 1) {
+            if (n3l) k_vl_build_warp<R, true, 1><<<wblocks, VL_WBUILD_THREADS, 0, st>>>(S);
+            else k_vl_build_warp<R, false, 1><<<wblocks, VL_WBUILD_THREADS, 0, st>>>(S);
+        } else {
+            if (n3l) k_vl_build_warp<R, true, 2><<<wblocks, VL_WBUILD_THREADS, 0, st>>>(S);
+            else k_vl_build_warp<R, false, 2><<<wblocks, VL_WBUILD_THREADS, 0, st>>>(S);
+        }
+        return;
+    }
     const int blocks = div_up(S.n, VL_BUILD_THREADS);
     if (S.reach == 1) {
         if (n3l) k_vl_build<R, true, 1><<<blocks, VL_BUILD_THREADS, 0, st>>>(S);
